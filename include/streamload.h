@@ -1,0 +1,222 @@
+/*
+ * streamload.h -- C ABI of the GB300 (sm_103a) streaming global-load library.
+ *
+ * The library measures how attained HBM bandwidth responds to offered load
+ * concurrency, the quantity studied by "Concurrency Response of Plain Global
+ * Loads on the NVIDIA H100" (arXiv 2608.15764).  One data-parallel hot path:
+ * every 16-byte vector of a device buffer is loaded exactly once per pass and
+ * folded into a checksum (paper §3 "Instruments": loaded values go into a sink
+ * so that no load is dead), with the total number of issued 16-byte loads held
+ * fixed across offered ILP K (paper §3 "Fixed-work control").  Three load
+ * mechanisms:
+ *
+ *   SL_LDG      plain ld.global: each thread issues K independent 16-byte
+ *               loads per iteration before consuming them (paper §3 "The axis
+ *               K"; §4.2 primary cell: .cg, 16 B).
+ *   SL_CPASYNC  cp.async 16-byte copies into shared memory with D commit
+ *               groups in flight (paper §4.3 compares cp.async with plain
+ *               loads).
+ *   SL_TMA      Blackwell bulk-async copies (cp.async.bulk) of whole stages
+ *               through an mbarrier ring (paper §2 names the TMA and bulk
+ *               copies; the paper has no TMA kernel, the ring is this
+ *               library's design).
+ *
+ * and two layered forms: float payloads (FP32 / BF16 / FP8-E4M3) summed with
+ * FP32 Kahan accumulation and an FP64 final combine, and a batched form (many
+ * buffers, one CUDA-graph launch) declared further below.
+ *
+ * Conventions for every function:
+ *   - Return an int status: SL_OK (0) or a negative SL_ERR_* code.  They never
+ *     abort, trap or print; sl_last_error() returns a message for the calling
+ *     thread's most recent failure.
+ *   - Device pointers are CUDA device addresses (e.g. torch tensor
+ *     data_ptr()) on the CURRENT device; the caller owns them and keeps them
+ *     alive until the call returns (sl_run, sl_sweep, sl_run_host) or until
+ *     the enqueued work completes (sl_enqueue).
+ *   - The library owns its scratch memory (per-warp partials, timestamps, an
+ *     error word, an L2-flush buffer, staging buffers, events), allocated
+ *     lazily per device and kept until process exit.  Calls that use scratch
+ *     on one device must be ordered: issue them from one host thread at a time
+ *     and on one stream at a time (work on two streams at once races on the
+ *     scratch).
+ *   - Byte counts must be multiples of 16 and buffers 16-byte aligned
+ *     (SL_ERR_ALIGN otherwise); a zero byte count is valid and gives an all-
+ *     zero result.
+ */
+#ifndef STREAMLOAD_H
+#define STREAMLOAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SL_OK              0
+#define SL_ERR_ARG        -1  /* null pointer, bad enum, K/D/stages/cta out of range */
+#define SL_ERR_ALIGN      -2  /* buffer not 16-byte aligned, bytes not a multiple of 16 */
+#define SL_ERR_INFEASIBLE -3  /* configuration cannot launch: shared memory or
+                                 registers exceed the limit, zero occupancy, or
+                                 stage size not 4/16/64 KiB */
+#define SL_ERR_TIMEOUT    -4  /* a bounded device wait gave up (TMA ring) */
+#define SL_ERR_CUDA       -5  /* a CUDA runtime error; see sl_last_error() */
+#define SL_ERR_OOM        -6  /* scratch allocation failed */
+#define SL_ERR_NODEV      -7  /* no CUDA device */
+
+/* ---- enums ------------------------------------------------------------ */
+typedef enum { SL_U32 = 0, SL_F32 = 1, SL_BF16 = 2, SL_FP8_E4M3 = 3 } sl_dtype;
+typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2 } sl_mech;
+typedef enum { SL_ASC = 0, SL_DESC = 1 } sl_order;
+/* LDG load flavour: SL_COP_CG is the paper's primary cell (ld.global.cg,
+ * §4.2); the other two ask L2 for 256-byte prefetch granules. */
+typedef enum { SL_COP_CG = 0, SL_COP_CG_L2_256 = 1, SL_COP_NC_NA_L2_256 = 2 } sl_cop;
+
+#define SL_MAX_K 16
+#define SL_MAX_D 8
+#define SL_MIN_STAGES 2
+#define SL_MAX_STAGES 8
+
+/* ---- launch configuration ---------------------------------------------- */
+typedef struct sl_config {
+    int32_t mech;        /* sl_mech */
+    int32_t k;           /* SL_LDG: K = independent 16-byte loads per thread per
+                            iteration, 1..16.  SL_CPASYNC: D = commit groups in
+                            flight per thread, 1..8.  SL_TMA: ignored. */
+    int32_t stage_bytes; /* SL_TMA: bytes per ring stage, 4096, 16384 or 65536 */
+    int32_t stages;      /* SL_TMA: ring depth, 2..8 */
+    int32_t cta;         /* threads per CTA that fold loads, a multiple of 32:
+                            32..1024 for LDG/CPASYNC (LDG with K > 8: up to 512);
+                            32..992 for TMA, which adds one producer warp. */
+    int32_t grid;        /* CTAs; <= 0 selects min(4, resident CTAs per SM) x SMs */
+    int32_t order;       /* sl_order: traversal direction over tiles (ASC walks
+                            tile 0 upward, DESC the last tile downward); never
+                            changes the result */
+    int32_t flush_l2;    /* nonzero: overwrite a scratch buffer of twice the L2
+                            size before the launch, outside the timed interval */
+    int32_t passes;      /* read the buffer this many times, >= 1 (0 means 1) */
+    int32_t cop;         /* sl_cop, SL_LDG only */
+    int32_t debug_flags; /* 0 in normal use; SL_DEBUG_TMA_SKIP_STAGE makes the
+                            TMA producer leave one stage unarmed so that the
+                            consumers' bounded wait expires (failure-detection
+                            test: the call returns SL_ERR_TIMEOUT and the CUDA
+                            context stays usable) */
+    int32_t reserved;
+    void*   stream;      /* cudaStream_t to launch on; NULL = legacy default stream */
+} sl_config;
+
+#define SL_DEBUG_TMA_SKIP_STAGE 1
+
+/* ---- results ----------------------------------------------------------- */
+typedef struct sl_result {
+    uint64_t xor_u64;         /* XOR of the little-endian uint64 words read */
+    uint64_t issued_loads;    /* 16-byte logical loads folded; = passes*bytes/16 */
+    uint64_t device_ns;       /* CUDA-event time of the load kernel (sl_run);
+                                 of the whole call (sl_run_host); 0 (sl_enqueue) */
+    uint64_t window_ns;       /* %globaltimer: first CTA start to last CTA end */
+    double   fsum;            /* float dtypes: sum of the decoded payload */
+    float    fsum_hi;         /* fsum as a float pair: hi = fl(fsum) */
+    float    fsum_lo;         /*                       lo = fl(fsum - hi) */
+    uint32_t sum_u32;         /* sum of the uint32 words read, mod 2^32 */
+    int32_t  status;          /* SL_OK or SL_ERR_TIMEOUT (device-reported) */
+    int32_t  grid;            /* CTAs launched */
+    int32_t  cta;             /* threads per CTA launched (TMA: incl. producer warp) */
+    int32_t  resident_per_sm; /* occupancy-API residency of this launch shape */
+    int32_t  smem_bytes;      /* dynamic shared memory per CTA */
+} sl_result;
+
+typedef struct sl_devinfo {
+    int32_t device;
+    int32_t sm_count;
+    int32_t cc_major;
+    int32_t cc_minor;
+    int64_t l2_bytes;
+    int64_t smem_per_block_optin;
+    int64_t smem_per_sm;
+    int64_t global_mem_bytes;
+    int32_t max_threads_per_sm;
+    int32_t regs_per_sm;
+    int32_t clock_khz;        /* 0 where the runtime no longer reports it */
+    int32_t mem_clock_khz;    /* 0 where the runtime no longer reports it */
+    int32_t mem_bus_bits;
+    int32_t driver_version;
+    int32_t runtime_version;
+    int32_t reserved;
+    char    name[256];
+} sl_devinfo;
+
+/* ---- device, errors ---------------------------------------------------- */
+
+/* Properties of the current device (paper §3 "Environment" capture). */
+int sl_device_info(sl_devinfo* out);
+
+/* Message of the calling thread's most recent failed call ("" if none).  The
+ * pointer stays valid until the next call from the same thread. */
+const char* sl_last_error(void);
+
+/* ---- inputs and cache state -------------------------------------------- */
+
+/* Fill a device buffer with the splitmix64 stream seeded with `seed`
+ * (Steele, Lea and Flood 2014; counter form: output m = mix(seed +
+ * (m+1)*0x9E3779B97F4A7C15)); uint32 word 2m / 2m+1 is the low / high half
+ * of output m.  `bytes` a multiple of 16.  Asynchronous on `stream`. */
+int sl_fill_splitmix64(void* dev_buf, uint64_t bytes, uint64_t seed, void* stream);
+
+/* Overwrite the library's L2-flush buffer (twice the L2 size) so that no part
+ * of a previously read buffer stays L2-resident.  Asynchronous on `stream`. */
+int sl_flush_l2(void* stream);
+
+/* ---- the streaming checksum ------------------------------------------- */
+
+/* Resolve a configuration without launching: fills grid, cta,
+ * resident_per_sm and smem_bytes of *out (other fields zero) or returns
+ * SL_ERR_ARG / SL_ERR_ALIGN / SL_ERR_INFEASIBLE.  Used by sweeps to record
+ * infeasible cells. */
+int sl_plan(uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out);
+
+/* One streaming pass set over dev_buf[0, bytes) (spec call
+ * sl_run(buf, bytes, dtype, mech, K or D, cta, grid, order) -> checksum,
+ * device ns, issued-load count).  Tiles: LDG and CPASYNC walk tiles of
+ * cta*K (or cta*D) 16-byte vectors, CTA b taking tiles b, b+grid, ...
+ * (paper §3: each warp's access is contiguous and fully coalesced at every
+ * K); load k of thread t reads vector tile*cta*K + k*cta + t; the last tile is
+ * guarded so that issued loads = passes*bytes/16 exactly at every K.  TMA
+ * walks stage-sized chunks the same way.  dtype selects the fold: SL_U32
+ * computes sum_u32 / xor_u64; float dtypes also compute fsum (per-thread FP32
+ * Kahan over per-vector sums, warp TwoSum, FP64 combine of per-warp
+ * partials).  Synchronous: returns after the result is on the host. */
+int sl_run(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+           sl_result* out);
+
+/* As sl_run but asynchronous on cfg->stream: enqueues [L2 flush], the load
+ * kernel and the combine kernel, which writes an sl_result (device_ns = 0,
+ * launch-shape fields filled by the host) to the DEVICE pointer dev_out
+ * (8-byte aligned).  Successive enqueues on one stream may share the
+ * library's scratch; enqueues on different streams at once race. */
+int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+               sl_result* dev_out);
+
+/* Sweep (paper §3 "Fixed-work control": run each K sweep ascending and
+ * reversed; the warm-up launch is excluded as in §3 "Hardware counters").
+ * Runs the ncells configurations in cell order (sweep_order = SL_ASC) or in
+ * reverse (SL_DESC); for each cell `warmup` discarded runs then `repeats`
+ * timed sl_run calls.  Row out[c*repeats + r] holds cell c's r-th repeat
+ * whatever the sweep order.  An infeasible cell fills its rows with status
+ * SL_ERR_INFEASIBLE and the sweep continues; a CUDA error stops it. */
+int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cells,
+             int32_t ncells, int32_t repeats, int32_t warmup, int32_t sweep_order,
+             sl_result* out);
+
+/* End-to-end form: the payload is in HOST memory (page-locked for full
+ * speed).  Copies it to a library-owned device staging ring in chunks of
+ * 256 MiB on a copy stream, overlapped with the load kernel on each chunk,
+ * then combines all chunks and copies the result back.  device_ns covers the
+ * whole call (first copy to result on the host).  Synchronous. */
+int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+                sl_result* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STREAMLOAD_H */

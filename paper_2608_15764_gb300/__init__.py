@@ -1,0 +1,164 @@
+"""GB300 (sm_103a) streaming global-load library: Python binding.
+
+The functions below carry the C ABI's names (include/streamload.h) and only
+marshal arguments; every step of the path -- loading, folding, reducing,
+timing -- runs in ``libstreamload.so``.  PyTorch is used for device memory and
+streams: pass CUDA tensors (or raw device addresses) and, optionally, a
+``torch.cuda.Stream``.
+
+    import torch, paper_2608_15764_gb300 as sl
+    buf = torch.empty(1 << 28, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(buf, seed=1)
+    r = sl.sl_run(buf, dtype=sl.SL_U32, cfg=sl.config("ldg", k=2, cta=256))
+    print(r.sum_u32, r.xor_u64, r.issued_loads, r.device_ns)
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._abi import (  # noqa: F401  (re-exported constants)
+    SL_ASC, SL_BF16, SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256, SL_CPASYNC,
+    SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
+    SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_MAX_D, SL_MAX_K,
+    SL_MAX_STAGES, SL_MIN_STAGES, SL_OK, SL_TMA, SL_U32, STATUS_NAMES, RESULT_BYTES, load, sl_config, sl_devinfo,
+    sl_result,
+)
+
+MECHS = {"ldg": SL_LDG, "cpasync": SL_CPASYNC, "tma": SL_TMA}
+DTYPES = {"u32": SL_U32, "f32": SL_F32, "bf16": SL_BF16, "fp8": SL_FP8_E4M3}
+ORDERS = {"asc": SL_ASC, "desc": SL_DESC}
+
+
+class SLError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status: int) -> int:
+    if status != SL_OK:
+        raise SLError(status, load().sl_last_error().decode(errors="replace"))
+    return status
+
+
+def _addr(buf) -> int:
+    if buf is None:
+        return 0
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        return int(buf.data_ptr())
+    if hasattr(buf, "ctypes"):  # numpy array (host memory)
+        return int(buf.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(buf).__name__}")
+
+
+def _nbytes(buf, nbytes):
+    if nbytes is not None:
+        return int(nbytes)
+    if hasattr(buf, "nbytes"):
+        return int(buf.nbytes)
+    if hasattr(buf, "element_size"):
+        return int(buf.numel() * buf.element_size())
+    raise TypeError("nbytes is required for a raw address")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream) or None
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None
+
+
+def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *, stage_bytes: int = 16384,
+           stages: int = 4, flush_l2: bool = False, passes: int = 1, cop: int = SL_COP_CG,
+           debug_flags: int = 0, stream=None) -> sl_config:
+    """Build an sl_config.  mech: "ldg" / "cpasync" / "tma" (or the enum);
+    k: K for LDG, depth D for cp.async; stage_bytes/stages for TMA."""
+    c = sl_config()
+    c.mech = MECHS[mech] if isinstance(mech, str) else int(mech)
+    c.k = int(k)
+    c.stage_bytes = int(stage_bytes)
+    c.stages = int(stages)
+    c.cta = int(cta)
+    c.grid = int(grid)
+    c.order = ORDERS[order] if isinstance(order, str) else int(order)
+    c.flush_l2 = int(bool(flush_l2))
+    c.passes = int(passes)
+    c.cop = int(cop)
+    c.debug_flags = int(debug_flags)
+    c.stream = _stream_handle(stream)
+    return c
+
+
+def _dtype(dtype) -> int:
+    return DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+
+
+def sl_device_info() -> dict:
+    info = sl_devinfo()
+    _check(load().sl_device_info(ctypes.byref(info)))
+    return info.as_dict()
+
+
+def sl_last_error() -> str:
+    return load().sl_last_error().decode(errors="replace")
+
+
+def sl_fill_splitmix64(buf, nbytes=None, seed: int = 1, stream=None) -> None:
+    _check(load().sl_fill_splitmix64(_addr(buf), _nbytes(buf, nbytes), seed, _stream_handle(stream)))
+
+
+def sl_flush_l2(stream=None) -> None:
+    _check(load().sl_flush_l2(_stream_handle(stream)))
+
+
+def sl_plan(nbytes: int, dtype=SL_U32, cfg: sl_config | None = None) -> sl_result:
+    """Resolve a configuration without launching; raises SLError if it is
+    infeasible or invalid."""
+    cfg = cfg or config()
+    r = sl_result()
+    _check(load().sl_plan(int(nbytes), _dtype(dtype), ctypes.byref(cfg), ctypes.byref(r)))
+    return r
+
+
+def sl_run(buf, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> sl_result:
+    cfg = cfg or config()
+    r = sl_result()
+    _check(load().sl_run(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), ctypes.byref(r)))
+    return r
+
+
+def sl_enqueue(buf, dev_out, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> None:
+    """Asynchronous form: dev_out is a device buffer of at least RESULT_BYTES
+    (one sl_result) that receives the result."""
+    cfg = cfg or config()
+    _check(load().sl_enqueue(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), _addr(dev_out)))
+
+
+def sl_sweep(buf, cells, nbytes=None, dtype=SL_U32, repeats: int = 1, warmup: int = 1,
+             sweep_order=SL_ASC) -> list[list[sl_result]]:
+    """Returns rows[cell][repeat] (in cell order whatever the sweep order)."""
+    n = len(cells)
+    arr = (sl_config * n)(*cells)
+    out = (sl_result * (n * repeats))()
+    order = ORDERS[sweep_order] if isinstance(sweep_order, str) else int(sweep_order)
+    _check(load().sl_sweep(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), arr, n, repeats, warmup, order, out))
+    return [[out[c * repeats + r] for r in range(repeats)] for c in range(n)]
+
+
+def sl_run_host(host_buf, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> sl_result:
+    """End-to-end form over a HOST buffer (numpy array, pinned torch tensor or
+    address)."""
+    cfg = cfg or config()
+    r = sl_result()
+    _check(load().sl_run_host(_addr(host_buf), _nbytes(host_buf, nbytes), _dtype(dtype), ctypes.byref(cfg),
+                              ctypes.byref(r)))
+    return r

@@ -1,0 +1,533 @@
+// api.cu -- host implementation of the C ABI declared in include/streamload.h.
+//
+// Validation, launch planning (occupancy and shared-memory feasibility),
+// per-device scratch, CUDA-event timing, sweeps and the host-buffer pipeline.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "sl_internal.h"
+
+namespace sl {
+const void* ldg_kernel_u32(int k, int cta, int cop);
+const void* ldg_kernel_f32(int k, int cta, int cop);
+const void* ldg_kernel_bf16(int k, int cta, int cop);
+const void* ldg_kernel_fp8(int k, int cta, int cop);
+
+const void* ldg_kernel(int dtype, int k, int cta, int cop) {
+    switch (dtype) {
+    case SL_U32: return ldg_kernel_u32(k, cta, cop);
+    case SL_F32: return ldg_kernel_f32(k, cta, cop);
+    case SL_BF16: return ldg_kernel_bf16(k, cta, cop);
+    case SL_FP8_E4M3: return ldg_kernel_fp8(k, cta, cop);
+    default: return nullptr;
+    }
+}
+}  // namespace sl
+
+namespace {
+
+using sl::KArgs;
+using sl::WarpPartial;
+
+constexpr int MAX_DEVICES = 64;
+constexpr uint64_t HOST_CHUNK = 256ull << 20;     // sl_run_host staging chunk
+constexpr uint64_t TIMEOUT_NS = 2000000000ull;     // per-wait bound, normal runs
+constexpr uint64_t DEBUG_TIMEOUT_NS = 50000000ull;  // per-wait bound, fault-injection runs
+constexpr int64_t MAX_GRID = 1 << 20;
+
+thread_local char g_err[1024] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? SL_ERR_OOM : SL_ERR_CUDA,           \
+                        "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,     \
+                        __LINE__);                                                            \
+    } while (0)
+
+struct FuncInfo {
+    int max_threads = 0;
+    size_t local_bytes = 0;  // per-thread local memory (register spills)
+    int regs = 0;            // registers per thread
+    size_t smem_attr = 0;  // dynamic shared memory limit already set
+};
+
+struct DevCtx {
+    bool ready = false;
+    int dev = -1;
+    sl_devinfo info{};
+    WarpPartial* parts = nullptr;
+    uint64_t parts_cap = 0;
+    uint64_t* tstamp = nullptr;
+    uint64_t ts_cap = 0;
+    uint32_t* err = nullptr;
+    sl_result* dres = nullptr;  // device result of sl_run / sl_run_host
+    sl_result* hres = nullptr;  // pinned host copy
+    void* flush = nullptr;
+    uint64_t flush_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void* stage[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    std::map<const void*, FuncInfo> funcs;
+    std::map<std::tuple<const void*, int, size_t>, int> occupancy;
+    std::recursive_mutex mu;
+};
+
+DevCtx g_ctx[MAX_DEVICES];
+std::mutex g_init_mu;
+
+int query_info(int dev, sl_devinfo* out) {
+    cudaDeviceProp p;
+    CUDA_TRY(cudaGetDeviceProperties(&p, dev));
+    std::memset(out, 0, sizeof *out);
+    out->device = dev;
+    out->sm_count = p.multiProcessorCount;
+    out->cc_major = p.major;
+    out->cc_minor = p.minor;
+    out->l2_bytes = p.l2CacheSize;
+    out->smem_per_block_optin = static_cast<int64_t>(p.sharedMemPerBlockOptin);
+    out->smem_per_sm = static_cast<int64_t>(p.sharedMemPerMultiprocessor);
+    out->global_mem_bytes = static_cast<int64_t>(p.totalGlobalMem);
+    out->max_threads_per_sm = p.maxThreadsPerMultiProcessor;
+    out->regs_per_sm = p.regsPerMultiprocessor;
+    int v = 0;
+    out->clock_khz = cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, dev) == cudaSuccess ? v : 0;
+    v = 0;
+    out->mem_clock_khz = cudaDeviceGetAttribute(&v, cudaDevAttrMemoryClockRate, dev) == cudaSuccess ? v : 0;
+    v = 0;
+    out->mem_bus_bits = cudaDeviceGetAttribute(&v, cudaDevAttrGlobalMemoryBusWidth, dev) == cudaSuccess ? v : 0;
+    (void)cudaGetLastError();
+    cudaDriverGetVersion(&out->driver_version);
+    cudaRuntimeGetVersion(&out->runtime_version);
+    std::snprintf(out->name, sizeof out->name, "%s", p.name);
+    return SL_OK;
+}
+
+// The context of the current device, initialised on first use.
+int get_ctx(DevCtx** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(SL_ERR_NODEV, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(SL_ERR_NODEV, "device index %d out of range", dev);
+    DevCtx* c = &g_ctx[dev];
+    std::lock_guard<std::mutex> g(g_init_mu);
+    if (!c->ready) {
+        c->dev = dev;
+        int rc = query_info(dev, &c->info);
+        if (rc) return rc;
+        CUDA_TRY(cudaMalloc(&c->err, sizeof(uint32_t)));
+        CUDA_TRY(cudaMemset(c->err, 0, sizeof(uint32_t)));
+        CUDA_TRY(cudaMalloc(&c->dres, sizeof(sl_result)));
+        CUDA_TRY(cudaMallocHost(&c->hres, sizeof(sl_result)));
+        CUDA_TRY(cudaEventCreate(&c->ev0));
+        CUDA_TRY(cudaEventCreate(&c->ev1));
+        c->flush_bytes = ((2 * static_cast<uint64_t>(c->info.l2_bytes)) + (1u << 20) - 1) & ~((1ull << 20) - 1);
+        if (c->flush_bytes < (64ull << 20)) c->flush_bytes = 64ull << 20;
+        CUDA_TRY(cudaMalloc(&c->flush, c->flush_bytes));
+        CUDA_TRY(cudaDeviceSynchronize());
+        c->ready = true;
+    }
+    *out = c;
+    return SL_OK;
+}
+
+// Grow the partial / timestamp scratch.  Growing waits for the device to go
+// idle first, since enqueued work may still use the old buffers.
+int ensure_scratch(DevCtx* c, uint64_t nparts, uint64_t nctas) {
+    if (nparts > c->parts_cap) {
+        uint64_t cap = std::max<uint64_t>(nparts, 1 << 16);
+        CUDA_TRY(cudaDeviceSynchronize());
+        if (c->parts) CUDA_TRY(cudaFree(c->parts));
+        c->parts = nullptr;
+        c->parts_cap = 0;
+        CUDA_TRY(cudaMalloc(&c->parts, cap * sizeof(WarpPartial)));
+        c->parts_cap = cap;
+    }
+    if (nctas > c->ts_cap) {
+        uint64_t cap = std::max<uint64_t>(nctas, 1 << 14);
+        CUDA_TRY(cudaDeviceSynchronize());
+        if (c->tstamp) CUDA_TRY(cudaFree(c->tstamp));
+        c->tstamp = nullptr;
+        c->ts_cap = 0;
+        CUDA_TRY(cudaMalloc(&c->tstamp, 2 * cap * sizeof(uint64_t)));
+        c->ts_cap = cap;
+    }
+    return SL_OK;
+}
+
+struct Plan {
+    const void* fn = nullptr;
+    int block = 0;            // threads per CTA launched
+    int64_t grid = 0;         // CTAs (0: nothing to launch)
+    size_t smem = 0;          // dynamic shared memory
+    int resident = 0;         // occupancy-API CTAs per SM
+    uint64_t warps = 0;       // folding warps per CTA
+    KArgs args{};
+};
+
+int func_info(DevCtx* c, const void* fn, size_t smem, FuncInfo** out) {
+    FuncInfo& fi = c->funcs[fn];
+    if (fi.max_threads == 0) {
+        cudaFuncAttributes fa;
+        CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+        fi.max_threads = fa.maxThreadsPerBlock;
+        fi.local_bytes = fa.localSizeBytes;
+        fi.regs = fa.numRegs;
+    }
+    if (smem > 48 * 1024 && fi.smem_attr < smem) {
+        CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        fi.smem_attr = smem;
+    }
+    *out = &fi;
+    return SL_OK;
+}
+
+int occupancy(DevCtx* c, const void* fn, int block, size_t smem, int* out) {
+    auto key = std::make_tuple(fn, block, smem);
+    auto it = c->occupancy.find(key);
+    if (it != c->occupancy.end()) {
+        *out = it->second;
+        return SL_OK;
+    }
+    int n = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem));
+    c->occupancy[key] = n;
+    *out = n;
+    return SL_OK;
+}
+
+int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, Plan* p) {
+    if (!cfg) return fail(SL_ERR_ARG, "cfg is NULL");
+    if (dtype < SL_U32 || dtype > SL_FP8_E4M3) return fail(SL_ERR_ARG, "bad dtype %d", dtype);
+    if ((bytes & 15u) != 0) return fail(SL_ERR_ALIGN, "bytes (%llu) not a multiple of 16", (unsigned long long)bytes);
+    if (bytes > 0 && !buf) return fail(SL_ERR_ARG, "buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(buf) & 15u) != 0) return fail(SL_ERR_ALIGN, "buffer not 16-byte aligned");
+    if (cfg->passes < 0) return fail(SL_ERR_ARG, "passes %d < 0", cfg->passes);
+    if (cfg->order != SL_ASC && cfg->order != SL_DESC) return fail(SL_ERR_ARG, "bad order %d", cfg->order);
+    const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
+    const int cta = cfg->cta;
+    if (cta < 32 || cta > 1024 || (cta & 31)) return fail(SL_ERR_ARG, "cta %d not a multiple of 32 in 32..1024", cta);
+
+    uint64_t tile_vec = 0;
+    *p = Plan{};
+    switch (cfg->mech) {
+    case SL_LDG:
+        if (cfg->k < 1 || cfg->k > SL_MAX_K) return fail(SL_ERR_ARG, "LDG K %d not in 1..%d", cfg->k, SL_MAX_K);
+        if (cfg->cop < SL_COP_CG || cfg->cop > SL_COP_NC_NA_L2_256) return fail(SL_ERR_ARG, "bad cop %d", cfg->cop);
+        p->fn = sl::ldg_kernel(dtype, cfg->k, cta, cfg->cop);
+        if (!p->fn)
+            return fail(SL_ERR_ARG, "no LDG kernel for dtype %d, K %d, cta %d, cop %d (cta must be 32/128/256/512/1024 "
+                        "for uint32, 128/256/512 for floats; cop 2 is uint32 only)", dtype, cfg->k, cta, cfg->cop);
+        p->block = cta;
+        p->smem = 0;
+        tile_vec = static_cast<uint64_t>(cta) * cfg->k;
+        p->warps = cta / 32;
+        break;
+    case SL_CPASYNC:
+        if (cfg->k < 1 || cfg->k > SL_MAX_D) return fail(SL_ERR_ARG, "cp.async depth %d not in 1..%d", cfg->k, SL_MAX_D);
+        p->fn = sl::cpasync_kernel(dtype, cfg->k);
+        p->block = cta;
+        p->smem = static_cast<size_t>(cfg->k) * cta * 16;
+        tile_vec = static_cast<uint64_t>(cta) * cfg->k;
+        p->warps = cta / 32;
+        break;
+    case SL_TMA:
+        if (cfg->stage_bytes != 4096 && cfg->stage_bytes != 16384 && cfg->stage_bytes != 65536)
+            return fail(SL_ERR_INFEASIBLE, "TMA stage size %d not 4096/16384/65536", cfg->stage_bytes);
+        if (cfg->stages < SL_MIN_STAGES || cfg->stages > SL_MAX_STAGES)
+            return fail(SL_ERR_ARG, "TMA stages %d not in %d..%d", cfg->stages, SL_MIN_STAGES, SL_MAX_STAGES);
+        if (cta > 992) return fail(SL_ERR_ARG, "TMA consumer threads %d > 992", cta);
+        p->fn = sl::tma_kernel(dtype);
+        p->block = cta + 32;
+        p->smem = static_cast<size_t>(cfg->stages) * cfg->stage_bytes;
+        tile_vec = static_cast<uint64_t>(cfg->stage_bytes) / 16;
+        p->warps = cta / 32;
+        break;
+    default:
+        return fail(SL_ERR_ARG, "bad mech %d", cfg->mech);
+    }
+    if (!p->fn) return fail(SL_ERR_ARG, "no kernel instantiated for this configuration");
+    if (p->smem > static_cast<size_t>(c->info.smem_per_block_optin))
+        return fail(SL_ERR_INFEASIBLE, "%zu bytes of shared memory exceed the %lld-byte per-block limit", p->smem,
+                    (long long)c->info.smem_per_block_optin);
+    FuncInfo* fi = nullptr;
+    int rc = func_info(c, p->fn, p->smem, &fi);
+    if (rc) return rc;
+    if (fi->local_bytes > 0)
+        return fail(SL_ERR_INFEASIBLE, "this kernel spills registers (%zu bytes of local memory per thread)",
+                    fi->local_bytes);
+    // K in-flight 16-byte loads need 4K registers.  Where the CTA size caps
+    // registers below that (CTA 1024 with large K), the compiler interleaves
+    // loads with folds and K would no longer be the offered ILP.
+    if (cfg->mech == SL_LDG && fi->regs < 4 * cfg->k + 16)
+        return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d loads in flight at cta %d",
+                    fi->regs, cfg->k, cta);
+    if (p->block > fi->max_threads)
+        return fail(SL_ERR_INFEASIBLE, "%d threads per CTA exceed this kernel's limit of %d", p->block,
+                    fi->max_threads);
+    rc = occupancy(c, p->fn, p->block, p->smem, &p->resident);
+    if (rc) return rc;
+    if (p->resident < 1) return fail(SL_ERR_INFEASIBLE, "configuration has zero occupancy");
+
+    const uint64_t nvec = bytes / 16;
+    const uint64_t ntiles = (nvec + tile_vec - 1) / tile_vec;
+    int64_t grid = cfg->grid;
+    if (grid <= 0) grid = static_cast<int64_t>(std::min(4, p->resident)) * c->info.sm_count;
+    if (grid > MAX_GRID) return fail(SL_ERR_ARG, "grid %lld > %lld", (long long)grid, (long long)MAX_GRID);
+    p->grid = nvec == 0 ? 0 : grid;
+    KArgs& a = p->args;
+    a.buf = buf;
+    a.nvec = nvec;
+    a.ntiles = ntiles;
+    a.total = ntiles * passes;
+    a.tile_vec = static_cast<uint32_t>(tile_vec);
+    a.desc = cfg->order == SL_DESC ? 1 : 0;
+    a.nst = cfg->mech == SL_TMA ? cfg->stages : 0;
+    a.debug = cfg->debug_flags;
+    a.timeout_ns = cfg->debug_flags ? DEBUG_TIMEOUT_NS : TIMEOUT_NS;
+    return SL_OK;
+}
+
+int launch(const Plan& p, cudaStream_t s) {
+    if (p.grid == 0) return SL_OK;
+    KArgs a = p.args;
+    void* args[] = {&a};
+    CUDA_TRY(cudaLaunchKernel(p.fn, dim3(static_cast<unsigned>(p.grid)), dim3(p.block), args, p.smem, s));
+    return SL_OK;
+}
+
+void fill_shape(const Plan& p, sl_result* r) {
+    r->grid = static_cast<int32_t>(p.grid);
+    r->cta = p.block;
+    r->resident_per_sm = p.resident;
+    r->smem_bytes = static_cast<int32_t>(p.smem);
+}
+
+// Enqueue [flush], events, the load kernel and the combine on stream s.
+int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+                   sl_result* dev_out, bool events, Plan* plan_out) {
+    Plan p;
+    int rc = make_plan(c, buf, bytes, dtype, cfg, &p);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid) * p.warps, static_cast<uint64_t>(p.grid));
+    if (rc) return rc;
+    p.args.parts = c->parts;
+    p.args.tstamp = c->tstamp;
+    p.args.err = c->err;
+    if (cfg->flush_l2) CUDA_TRY(sl::launch_flush(c->flush, c->flush_bytes / 16, c->info.sm_count, s));
+    if (events) CUDA_TRY(cudaEventRecord(c->ev0, s));
+    rc = launch(p, s);
+    if (rc) return rc;
+    if (events) CUDA_TRY(cudaEventRecord(c->ev1, s));
+    CUDA_TRY(sl::launch_combine(c->parts, static_cast<uint64_t>(p.grid) * p.warps, c->tstamp,
+                                static_cast<uint64_t>(p.grid), c->err, dev_out, s));
+    if (plan_out) *plan_out = p;
+    return SL_OK;
+}
+
+int run_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
+    Plan p;
+    int rc = enqueue_locked(c, buf, bytes, dtype, cfg, c->dres, true, &p);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+    CUDA_TRY(cudaMemcpyAsync(c->hres, c->dres, sizeof(sl_result), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    *out = *c->hres;
+    out->device_ns = static_cast<uint64_t>(static_cast<double>(ms) * 1e6 + 0.5);
+    fill_shape(p, out);
+    if (out->status != SL_OK) return fail(out->status, "a bounded device wait timed out");
+    return SL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sl_last_error(void) { return g_err; }
+
+int sl_device_info(sl_devinfo* out) {
+    if (!out) return fail(SL_ERR_ARG, "out is NULL");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    *out = c->info;
+    return SL_OK;
+}
+
+int sl_fill_splitmix64(void* dev_buf, uint64_t bytes, uint64_t seed, void* stream) {
+    if ((bytes & 15u) != 0 || (reinterpret_cast<uintptr_t>(dev_buf) & 15u) != 0)
+        return fail(SL_ERR_ALIGN, "fill needs a 16-byte aligned buffer and a multiple of 16 bytes");
+    if (bytes > 0 && !dev_buf) return fail(SL_ERR_ARG, "buffer is NULL");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    CUDA_TRY(sl::launch_fill_splitmix64(dev_buf, bytes / 16, seed, c->info.sm_count, static_cast<cudaStream_t>(stream)));
+    return SL_OK;
+}
+
+int sl_flush_l2(void* stream) {
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    CUDA_TRY(sl::launch_flush(c->flush, c->flush_bytes / 16, c->info.sm_count, static_cast<cudaStream_t>(stream)));
+    return SL_OK;
+}
+
+int sl_plan(uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
+    if (!out) return fail(SL_ERR_ARG, "out is NULL");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    Plan p;
+    // a dummy aligned address: planning never dereferences the buffer
+    rc = make_plan(c, reinterpret_cast<const void*>(uintptr_t(256)), bytes, dtype, cfg, &p);
+    std::memset(out, 0, sizeof *out);
+    if (rc) {
+        out->status = rc;
+        return rc;
+    }
+    fill_shape(p, out);
+    if (p.grid == 0) {
+        // empty buffer: report the shape a non-empty one would get
+        int64_t grid = cfg->grid > 0 ? cfg->grid : static_cast<int64_t>(std::min(4, p.resident)) * c->info.sm_count;
+        out->grid = static_cast<int32_t>(grid);
+    }
+    return SL_OK;
+}
+
+int sl_run(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
+    if (!out) return fail(SL_ERR_ARG, "out is NULL");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    return run_locked(c, dev_buf, bytes, dtype, cfg, out);
+}
+
+int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* dev_out) {
+    if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u)) return fail(SL_ERR_ARG, "dev_out NULL or misaligned");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    return enqueue_locked(c, dev_buf, bytes, dtype, cfg, dev_out, false, nullptr);
+}
+
+int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cells, int32_t ncells,
+             int32_t repeats, int32_t warmup, int32_t sweep_order, sl_result* out) {
+    if (!cells || !out || ncells < 0 || repeats < 1 || warmup < 0)
+        return fail(SL_ERR_ARG, "bad sweep arguments");
+    if (sweep_order != SL_ASC && sweep_order != SL_DESC) return fail(SL_ERR_ARG, "bad sweep order");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    for (int32_t j = 0; j < ncells; ++j) {
+        const int32_t cell = sweep_order == SL_ASC ? j : ncells - 1 - j;
+        sl_result* row = out + static_cast<int64_t>(cell) * repeats;
+        sl_result tmp;
+        int st = SL_OK;
+        for (int32_t w = 0; w < warmup && st == SL_OK; ++w) st = run_locked(c, dev_buf, bytes, dtype, &cells[cell], &tmp);
+        for (int32_t r = 0; r < repeats; ++r) {
+            if (st == SL_OK) st = run_locked(c, dev_buf, bytes, dtype, &cells[cell], &row[r]);
+            if (st != SL_OK) {
+                std::memset(&row[r], 0, sizeof row[r]);
+                row[r].status = st;
+            }
+        }
+        if (st == SL_ERR_CUDA || st == SL_ERR_OOM || st == SL_ERR_NODEV) return st;
+    }
+    return SL_OK;
+}
+
+int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
+    if (!out || !cfg) return fail(SL_ERR_ARG, "NULL argument");
+    if (bytes > 0 && !host_buf) return fail(SL_ERR_ARG, "host buffer is NULL");
+    if ((bytes & 15u) != 0) return fail(SL_ERR_ALIGN, "bytes not a multiple of 16");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+    if (!c->stage[0]) {
+        for (int b = 0; b < 2; ++b) {
+            CUDA_TRY(cudaMalloc(&c->stage[b], HOST_CHUNK));
+            CUDA_TRY(cudaEventCreateWithFlags(&c->copied[b], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&c->consumed[b], cudaEventDisableTiming));
+        }
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    }
+    const uint64_t chunk = std::min<uint64_t>(bytes, HOST_CHUNK);
+    const uint64_t nchunks = bytes == 0 ? 0 : (bytes + HOST_CHUNK - 1) / HOST_CHUNK;
+    // One launch shape for every chunk (planned on a full chunk), so every
+    // chunk's kernel writes all of its partial slots.
+    Plan p;
+    rc = make_plan(c, c->stage[0], chunk, dtype, cfg, &p);
+    if (rc) return rc;
+    const uint64_t per_parts = static_cast<uint64_t>(p.grid) * p.warps;
+    rc = ensure_scratch(c, per_parts * nchunks, static_cast<uint64_t>(p.grid) * nchunks);
+    if (rc) return rc;
+    const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
+
+    CUDA_TRY(cudaEventRecord(c->ev0, s));
+    CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->ev0, 0));
+    for (uint64_t i = 0; i < nchunks; ++i) {
+        const int b = static_cast<int>(i & 1);
+        const uint64_t off = i * HOST_CHUNK;
+        const uint64_t len = std::min<uint64_t>(HOST_CHUNK, bytes - off);
+        if (i >= 2) CUDA_TRY(cudaStreamWaitEvent(c->copy_stream, c->consumed[b], 0));
+        CUDA_TRY(cudaMemcpyAsync(c->stage[b], static_cast<const uint8_t*>(host_buf) + off, len,
+                                 cudaMemcpyHostToDevice, c->copy_stream));
+        CUDA_TRY(cudaEventRecord(c->copied[b], c->copy_stream));
+        CUDA_TRY(cudaStreamWaitEvent(s, c->copied[b], 0));
+        KArgs a = p.args;
+        const uint64_t nvec = len / 16;
+        a.buf = c->stage[b];
+        a.nvec = nvec;
+        a.ntiles = (nvec + a.tile_vec - 1) / a.tile_vec;
+        a.total = a.ntiles * passes;
+        a.parts = c->parts + i * per_parts;
+        a.tstamp = c->tstamp + 2 * i * static_cast<uint64_t>(p.grid);
+        a.err = c->err;
+        void* args[] = {&a};
+        CUDA_TRY(cudaLaunchKernel(p.fn, dim3(static_cast<unsigned>(p.grid)), dim3(p.block), args, p.smem, s));
+        CUDA_TRY(cudaEventRecord(c->consumed[b], s));
+    }
+    CUDA_TRY(sl::launch_combine(c->parts, per_parts * nchunks, c->tstamp, static_cast<uint64_t>(p.grid) * nchunks,
+                                c->err, c->dres, s));
+    CUDA_TRY(cudaMemcpyAsync(c->hres, c->dres, sizeof(sl_result), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaEventRecord(c->ev1, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    *out = *c->hres;
+    out->device_ns = static_cast<uint64_t>(static_cast<double>(ms) * 1e6 + 0.5);
+    fill_shape(p, out);
+    if (nchunks == 0) out->grid = 0;
+    if (out->status != SL_OK) return fail(out->status, "a bounded device wait timed out");
+    return SL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// k_ldg.cuh -- the plain-load (LDG) streaming kernel.
+//
+// Paper §3 "The axis K": K is the number of independent ld.global
+// instructions a thread issues per iteration before consuming them.  Paper §3
+// "Fixed-work control": total issued logical loads are the same at every K;
+// here exactly one 16-byte load per 16 bytes per pass (the last tile is
+// guarded instead of rounding the iteration count).  Each warp instruction
+// reads 32 consecutive 16-byte vectors (512 contiguous bytes), so every
+// warp's access is contiguous and fully coalesced at every K.
+//
+// Tile = cta*K vectors.  CTA b walks tiles b, b+grid, b+2*grid, ... over all
+// passes (tile index taken mod the tiles per pass; reversed for SL_DESC).
+// Load k of thread t reads vector tile*cta*K + k*cta + t.
+#pragma once
+
+#include "sl_device.cuh"
+
+namespace sl {
+
+template <int K, int CTA, int DT, int COP>
+__global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
+    // launch_bounds(CTA, 1) lets ptxas keep all K loaded vectors in registers
+    // (4K registers) instead of interleaving loads with folds to save
+    // registers; configurations whose kernel would spill are rejected on the
+    // host (local memory > 0), as the paper requires zero spills (§3).
+    constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
+    const uint64_t t0 = gtimer();
+    const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
+    const uint64_t ntiles = a.ntiles;
+    const bool last_full = (a.nvec == ntiles * TILE);
+    Acc<DT> acc;
+    uint32_t full_iters = 0;
+    TileCursor c;
+    c.start(ntiles);
+#pragma unroll 1
+    for (; c.it < a.total; c.next(ntiles)) {
+        const uint64_t tile = c.tile(a);
+        const uint4* p = buf + tile * TILE + threadIdx.x;
+        uint4 v[K];
+        if (last_full || tile + 1 < ntiles) {
+            // K independent loads issued back to back, then consumed.
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = ldg16<COP>(p + k * CTA);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc.fold(v[k]);
+            ++full_iters;
+        } else {
+            // Ragged last tile: only vectors below nvec are loaded.
+            const uint32_t rem = static_cast<uint32_t>(a.nvec - tile * TILE);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (threadIdx.x + k * CTA < rem) v[k] = ldg16<COP>(p + k * CTA);
+                else v[k] = make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (threadIdx.x + k * CTA < rem) {
+                    acc.fold(v[k]);
+                    acc.n += 1;
+                }
+            }
+        }
+    }
+    acc.n += static_cast<uint64_t>(full_iters) * K;
+    warp_store<DT>(acc, a.parts + static_cast<uint64_t>(blockIdx.x) * (CTA / 32) + (threadIdx.x >> 5));
+    cta_stamp(a, t0);
+}
+
+}  // namespace sl
+
+// Table of instantiations K = 1..16 x CTA sizes x load flavours for one dtype.
+#define SL_LDG_K_CASES(FN, ...)                                                        \
+    switch (k) {                                                                       \
+    case 1: return FN<1, __VA_ARGS__>();  case 2: return FN<2, __VA_ARGS__>();             \
+    case 3: return FN<3, __VA_ARGS__>();  case 4: return FN<4, __VA_ARGS__>();             \
+    case 5: return FN<5, __VA_ARGS__>();  case 6: return FN<6, __VA_ARGS__>();             \
+    case 7: return FN<7, __VA_ARGS__>();  case 8: return FN<8, __VA_ARGS__>();             \
+    case 9: return FN<9, __VA_ARGS__>();  case 10: return FN<10, __VA_ARGS__>();           \
+    case 11: return FN<11, __VA_ARGS__>(); case 12: return FN<12, __VA_ARGS__>();          \
+    case 13: return FN<13, __VA_ARGS__>(); case 14: return FN<14, __VA_ARGS__>();          \
+    case 15: return FN<15, __VA_ARGS__>(); case 16: return FN<16, __VA_ARGS__>();          \
+    default: return nullptr;                                                           \
+    }
+
+namespace sl {
+template <int K, int CTA, int DT, int COP>
+const void* ldg_ptr() { return reinterpret_cast<const void*>(&k_ldg<K, CTA, DT, COP>); }
+
+template <int CTA, int DT, int COP>
+const void* ldg_pick_k(int k) { SL_LDG_K_CASES(ldg_ptr, CTA, DT, COP) }
+}  // namespace sl

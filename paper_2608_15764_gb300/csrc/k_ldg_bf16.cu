@@ -1,0 +1,23 @@
+// k_ldg_bf16.cu -- LDG kernel instantiations for SL_BF16 payloads:
+// K = 1..16, CTA = 128/256/512, load flavours .cg and .cg.L2::256B.
+#include "k_ldg.cuh"
+
+namespace sl {
+template <int COP>
+static const void* pick_cta(int k, int cta) {
+    switch (cta) {
+    case 128: return ldg_pick_k<128, SL_BF16, COP>(k);
+    case 256: return ldg_pick_k<256, SL_BF16, COP>(k);
+    case 512: return ldg_pick_k<512, SL_BF16, COP>(k);
+    default: return nullptr;
+    }
+}
+
+const void* ldg_kernel_bf16(int k, int cta, int cop) {
+    switch (cop) {
+    case SL_COP_CG: return pick_cta<SL_COP_CG>(k, cta);
+    case SL_COP_CG_L2_256: return pick_cta<SL_COP_CG_L2_256>(k, cta);
+    default: return nullptr;
+    }
+}
+}  // namespace sl

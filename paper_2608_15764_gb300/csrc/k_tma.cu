@@ -1,0 +1,175 @@
+// k_tma.cu -- the TMA (bulk asynchronous copy) streaming kernel.
+//
+// The paper names Hopper's TMA and bulk-asynchronous copies (§2) but has no
+// TMA kernel; this ring is the library's own Blackwell design.
+//
+// CTA = one producer warp + `cta` consumer threads.  The buffer is cut into
+// stage-sized chunks (stage_bytes, the last one ragged); CTA b takes chunks
+// b, b+grid, ... over all passes (reversed for SL_DESC).  Lane 0 of warp 0
+// owns a ring of `nst` stages in dynamic shared memory with two mbarriers per
+// stage:
+//   full[s]  count 1: the producer arms it with arrive.expect_tx(bytes) and
+//            issues one cp.async.bulk global->shared that completes the
+//            transaction bytes;
+//   empty[s] count = consumer warps: each consumer warp arrives once it has
+//            read the stage.
+// The producer waits on empty[s] before refilling stage s; consumers wait on
+// full[s], read the stage with ld.shared.v4 (thread t takes vectors t,
+// t+cta, ...) and fold.  No multicast is used anywhere.
+//
+// Every wait is bounded: a wait that exceeds a.timeout_ns (by %globaltimer)
+// or a hard iteration cap records an error code in *a.err, raises the CTA's
+// abort flag and returns false.  Waiters also give up when they see the abort
+// flag.  Before exiting after an abort, the producer waits (bounded) for
+// every bulk copy it issued to land (it does so on every exit), so no copy is
+// in flight into shared memory when the CTA exits.  A consumer warp leaves
+// the ring only when all its lanes agree (__all_sync), so warp-wide shuffles
+// after the loop see every lane.
+#include "sl_device.cuh"
+
+namespace sl {
+
+constexpr uint32_t WAIT_ITER_CAP = 1u << 26;
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Bounded wait for the phase of `bar` with the given parity to complete.
+// Returns false on timeout (after recording `code`) or when the abort flag is
+// seen (if watch_abort).
+__device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, const KArgs& a,
+                                             volatile int* abort_flag, bool watch_abort,
+                                             uint32_t code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t start = gtimer();
+    for (uint32_t n = 0; n < WAIT_ITER_CAP; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (watch_abort && *abort_flag) return false;
+        if (gtimer() - start > a.timeout_ns) break;
+    }
+    atomicCAS(a.err, 0u, code);
+    *abort_flag = 1;
+    return false;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
+    extern __shared__ __align__(128) uint8_t ring[];
+    __shared__ __align__(8) uint64_t full[SL_MAX_STAGES];
+    __shared__ __align__(8) uint64_t empty[SL_MAX_STAGES];
+    __shared__ volatile int abort_flag;
+
+    const uint64_t t0 = gtimer();
+    const uint32_t nst = static_cast<uint32_t>(a.nst);
+    const uint32_t stage_bytes = a.tile_vec * 16u;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t ncw = (blockDim.x >> 5) - 1;  // consumer warps
+    const uint64_t bytes = a.nvec * 16ull;
+    const uint8_t* __restrict__ gbuf = static_cast<const uint8_t*>(a.buf);
+    const uint32_t ring0 = smem_addr(ring);
+    const uint32_t full0 = smem_addr(full), empty0 = smem_addr(empty);
+
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < nst; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, ncw);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    Acc<DT> acc;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer ----
+            uint32_t armed = 0;     // bit s: stage s has had a copy issued
+            uint32_t last_par = 0;  // bit s: parity of the round of stage s's last copy
+            TileCursor c;
+            c.start(a.ntiles);
+            uint32_t s = 0, r = 0;  // stage and round of chunk i = r*nst + s
+            for (uint64_t i = 0; c.it < a.total; c.next(a.ntiles), ++i) {
+                if (r > 0 && !bounded_wait(empty0 + 8 * s, (r - 1) & 1u, a, &abort_flag, true,
+                                           DEV_ERR_TIMEOUT_EMPTY))
+                    break;
+                const uint64_t off = c.tile(a) * stage_bytes;
+                const uint64_t left = bytes - off;
+                const uint32_t len = left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes;
+                if (!((a.debug & SL_DEBUG_TMA_SKIP_STAGE) && i == 1)) {  // debug: leave chunk 1 unarmed
+                    mbar_arrive_expect_tx(full0 + 8 * s, len);
+                    bulk_g2s(ring0 + s * stage_bytes, gbuf + off, len, full0 + 8 * s);
+                    armed |= 1u << s;
+                    last_par = (last_par & ~(1u << s)) | ((r & 1u) << s);
+                }
+                if (++s == nst) { s = 0; ++r; }
+            }
+            // Drain: every issued copy must have landed before the CTA exits
+            // (immediate in normal operation; bounded after an abort).
+            {
+                for (uint32_t s = 0; s < nst; ++s)
+                    if (armed & (1u << s))
+                        bounded_wait(full0 + 8 * s, (last_par >> s) & 1u, a, &abort_flag, false,
+                                     DEV_ERR_TIMEOUT_DRAIN);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- consumers ----
+        const uint32_t ct = threadIdx.x - 32, nct = ncw * 32;
+        TileCursor c;
+        c.start(a.ntiles);
+        uint32_t s = 0, r = 0;
+        for (; c.it < a.total; c.next(a.ntiles)) {
+            const bool got = bounded_wait(full0 + 8 * s, r & 1u, a, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
+            if (!__all_sync(FULL_MASK, got)) break;  // warp-uniform exit
+            const uint64_t off = c.tile(a) * stage_bytes;
+            const uint64_t left = bytes - off;
+            const uint32_t nv = (left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes) >> 4;
+            const uint32_t base = ring0 + s * stage_bytes;
+#pragma unroll 4
+            for (uint32_t v = ct; v < nv; v += nct) {
+                acc.fold(lds16(base + 16u * v));
+                acc.n += 1;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * s);
+            if (++s == nst) { s = 0; ++r; }
+        }
+        warp_store<DT>(acc, a.parts + static_cast<uint64_t>(blockIdx.x) * ncw + (warp - 1));
+    }
+    cta_stamp(a, t0);
+}
+
+const void* tma_kernel(int dtype) {
+    switch (dtype) {
+    case SL_U32: return reinterpret_cast<const void*>(&k_tma<SL_U32>);
+    case SL_F32: return reinterpret_cast<const void*>(&k_tma<SL_F32>);
+    case SL_BF16: return reinterpret_cast<const void*>(&k_tma<SL_BF16>);
+    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&k_tma<SL_FP8_E4M3>);
+    default: return nullptr;
+    }
+}
+
+}  // namespace sl

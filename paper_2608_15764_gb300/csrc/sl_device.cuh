@@ -1,0 +1,207 @@
+// sl_device.cuh -- device-side building blocks of the streaming-load kernels:
+// 16-byte global loads, the checksum / compensated-sum fold, warp reduction
+// and per-warp partial output.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sl_internal.h"
+
+namespace sl {
+
+constexpr unsigned FULL_MASK = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One 16-byte global load (paper §3: one ld.global per offered load; §4.2
+// primary cell uses .cg, which caches in L2 only).  volatile keeps every load
+// in the program and in source order.
+template <int COP>
+__device__ __forceinline__ uint4 ldg16(const uint4* p) {
+    uint4 v;
+    if constexpr (COP == SL_COP_CG) {
+        asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    } else if constexpr (COP == SL_COP_CG_L2_256) {
+        asm volatile("ld.global.cg.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    } else {
+        asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds16(uint32_t saddr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(saddr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- per-vector float sums -------------------------------------------------
+// float32: 4 values, pairwise.
+__device__ __forceinline__ float vec_sum_f32(const uint4& v) {
+    return (__uint_as_float(v.x) + __uint_as_float(v.y)) +
+           (__uint_as_float(v.z) + __uint_as_float(v.w));
+}
+
+// bfloat16: 8 values.  add.f32.bf16 widens its bf16 operand exactly and rounds
+// once in FP32, so each step is one FP32 addition of the decoded value.
+__device__ __forceinline__ float vec_sum_bf16(const uint4& v) {
+    float a = __uint_as_float(v.y & 0xFFFF0000u);  // high half of word 1
+    float b = __uint_as_float(v.w & 0xFFFF0000u);  // high half of word 3
+    asm("{\n\t.reg .b16 l0, h0, l1, h1;\n\t"
+        "mov.b32 {l0, h0}, %1;\n\t"
+        "mov.b32 {l1, h1}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l0, %0;\n\t"
+        "add.rn.f32.bf16 %0, h0, %0;\n\t"
+        "add.rn.f32.bf16 %0, l1, %0;\n\t}"
+        : "+f"(a) : "r"(v.x), "r"(v.y));
+    asm("{\n\t.reg .b16 l0, h0, l1, h1;\n\t"
+        "mov.b32 {l0, h0}, %1;\n\t"
+        "mov.b32 {l1, h1}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l0, %0;\n\t"
+        "add.rn.f32.bf16 %0, h0, %0;\n\t"
+        "add.rn.f32.bf16 %0, l1, %0;\n\t}"
+        : "+f"(b) : "r"(v.z), "r"(v.w));
+    return a + b;
+}
+
+// FP8 E4M3: 16 values.  cvt.rn.f16x2.e4m3x2 widens two codes to half exactly
+// (every E4M3 value is a half), add.f32.f16 adds a half to an FP32
+// accumulator.  Every E4M3 value is an integer multiple of 2^-9 below 2^9, so
+// any partial sum of 16 of them is a multiple of 2^-9 below 2^13 and fits the
+// 24-bit FP32 significand: the per-vector sum is exact in any order.
+__device__ __forceinline__ float fp8_word_sum(uint32_t w, float acc) {
+    asm("{\n\t.reg .b16 q0, q1, a0, a1, b0, b1;\n\t.reg .b32 h0, h1;\n\t"
+        "mov.b32 {q0, q1}, %1;\n\t"
+        "cvt.rn.f16x2.e4m3x2 h0, q0;\n\t"
+        "cvt.rn.f16x2.e4m3x2 h1, q1;\n\t"
+        "mov.b32 {a0, a1}, h0;\n\t"
+        "mov.b32 {b0, b1}, h1;\n\t"
+        "add.rn.f32.f16 %0, a0, %0;\n\t"
+        "add.rn.f32.f16 %0, a1, %0;\n\t"
+        "add.rn.f32.f16 %0, b0, %0;\n\t"
+        "add.rn.f32.f16 %0, b1, %0;\n\t}"
+        : "+f"(acc) : "r"(w));
+    return acc;
+}
+
+__device__ __forceinline__ float vec_sum_fp8(const uint4& v) {
+    float a = fp8_word_sum(v.y, fp8_word_sum(v.x, 0.0f));
+    float b = fp8_word_sum(v.w, fp8_word_sum(v.z, 0.0f));
+    return a + b;
+}
+
+template <int DT>
+__device__ __forceinline__ float vec_sum(const uint4& v) {
+    if constexpr (DT == SL_F32) return vec_sum_f32(v);
+    else if constexpr (DT == SL_BF16) return vec_sum_bf16(v);
+    else return vec_sum_fp8(v);
+}
+
+// ---- the fold ----------------------------------------------------------------
+// Per-thread accumulator.  Integer part (every dtype): wraparound uint32 sum
+// of the four words and XOR of the two little-endian uint64 halves.  Float
+// part (float dtypes): FP32 Kahan summation of the per-vector sums; the
+// represented value is ks - kc.
+template <int DT>
+struct Acc {
+    uint32_t s = 0, xl = 0, xh = 0;
+    uint64_t n = 0;
+    float ks = 0.0f, kc = 0.0f;
+
+    __device__ __forceinline__ void fold(const uint4& v) {
+        s += (v.x + v.y) + (v.z + v.w);
+        xl ^= v.x ^ v.z;
+        xh ^= v.y ^ v.w;
+        if constexpr (DT != SL_U32) {
+            const float p = vec_sum<DT>(v);
+            const float y = p - kc;
+            const float t = ks + y;
+            kc = (t - ks) - y;
+            ks = t;
+        }
+    }
+};
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Reduce the warp's accumulators (shuffle butterfly; float pairs combined as
+// double-float with TwoSum) and let lane 0 store the warp partial.
+template <int DT>
+__device__ __forceinline__ void warp_store(const Acc<DT>& a, WarpPartial* dst) {
+    uint32_t s = a.s, xl = a.xl, xh = a.xh;
+    uint64_t n = a.n;
+    float hi = a.ks, lo = -a.kc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(FULL_MASK, s, o);
+        xl ^= __shfl_xor_sync(FULL_MASK, xl, o);
+        xh ^= __shfl_xor_sync(FULL_MASK, xh, o);
+        n += __shfl_xor_sync(FULL_MASK, n, o);
+        if constexpr (DT != SL_U32) {
+            const float ohi = __shfl_xor_sync(FULL_MASK, hi, o);
+            const float olo = __shfl_xor_sync(FULL_MASK, lo, o);
+            float sh, se;
+            two_sum(hi, ohi, sh, se);
+            se += lo + olo;
+            hi = sh + se;
+            lo = se - (hi - sh);
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        WarpPartial p;
+        p.sum = s;
+        p.pad = 0;
+        p.xr = (static_cast<uint64_t>(xh) << 32) | xl;
+        p.issued = n;
+        p.hi = hi;
+        p.lo = lo;
+        *dst = p;
+    }
+}
+
+// Tile cursor over the grid-stride sequence it = blockIdx.x, +gridDim.x, ...
+// tm = it mod ntiles (the pass-local tile), tracked without division.
+struct TileCursor {
+    uint64_t it, tm;
+    __device__ __forceinline__ void start(uint64_t ntiles) {
+        it = blockIdx.x;
+        tm = blockIdx.x % ntiles;
+    }
+    __device__ __forceinline__ void next(uint64_t ntiles) {
+        it += gridDim.x;
+        tm += gridDim.x;
+        while (tm >= ntiles) tm -= ntiles;
+    }
+    __device__ __forceinline__ uint64_t tile(const KArgs& a) const {
+        return a.desc ? (a.ntiles - 1 - tm) : tm;
+    }
+};
+
+// Store the CTA's start/end %globaltimer stamps (after every thread is done).
+__device__ __forceinline__ void cta_stamp(const KArgs& a, uint64_t t0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.tstamp[2 * blockIdx.x] = t0;
+        a.tstamp[2 * blockIdx.x + 1] = gtimer();
+    }
+}
+
+}  // namespace sl

@@ -1,0 +1,57 @@
+// sl_internal.h -- definitions shared by the host API and the kernels of the
+// streaming-load library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/streamload.h"
+
+namespace sl {
+
+// One warp's folded contribution.  The final combine adds sum (mod 2^32),
+// XORs xr, adds issued, and adds (double)hi + (double)lo in FP64.
+struct __align__(16) WarpPartial {
+    uint32_t sum;
+    uint32_t pad;
+    uint64_t xr;
+    uint64_t issued;
+    float hi;
+    float lo;
+};
+static_assert(sizeof(WarpPartial) == 32, "WarpPartial layout");
+
+// Arguments of every streaming kernel (passed by value as one struct).
+struct KArgs {
+    const void* buf;        // device buffer base, 16-byte aligned
+    uint64_t nvec;          // 16-byte vectors in the buffer
+    uint64_t ntiles;        // tiles per pass
+    uint64_t total;         // tiles over all passes = ntiles * passes
+    uint32_t tile_vec;      // 16-byte vectors per tile (LDG: cta*K, CPASYNC: cta*D,
+                            // TMA: stage_bytes/16)
+    int32_t desc;           // 1: walk tiles from the last one downward
+    int32_t nst;            // TMA: ring stages
+    int32_t debug;          // SL_DEBUG_* flags
+    WarpPartial* parts;     // [grid * folding warps per CTA]
+    uint64_t* tstamp;       // [2 * grid]: %globaltimer at CTA start / end
+    uint32_t* err;          // device error word (0 = fine)
+    uint64_t timeout_ns;    // bound of any single device wait
+};
+
+// Device error codes written to *err (first writer wins).
+enum : uint32_t { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT_FULL = 1, DEV_ERR_TIMEOUT_EMPTY = 2,
+                  DEV_ERR_TIMEOUT_DRAIN = 3 };
+
+// Kernel lookup.  Each returns the __global__ function for the given
+// instantiation, or nullptr when out of range.  All take (KArgs).
+const void* ldg_kernel(int dtype, int k, int cta, int cop);
+const void* cpasync_kernel(int dtype, int d);
+const void* tma_kernel(int dtype);
+
+// Utility launches (k_util.cu); asynchronous on `s`.
+cudaError_t launch_fill_splitmix64(void* buf, uint64_t nvec, uint64_t seed, int sms, cudaStream_t s);
+cudaError_t launch_flush(void* buf, uint64_t nvec, int sms, cudaStream_t s);
+cudaError_t launch_combine(const WarpPartial* parts, uint64_t nparts, const uint64_t* tstamp,
+                           uint64_t nctas, uint32_t* err, sl_result* out, cudaStream_t s);
+
+}  // namespace sl

@@ -1,0 +1,108 @@
+"""Response-curve measurement and configuration choice.
+
+A curve is attained GB/s per offered-concurrency point of one mechanism
+(LDG: K; cp.async: depth D; TMA: stage size x stages) on one buffer.  The
+choice rule picks the point with the highest median GB/s; points within
+``tie_frac`` of the best count as ties, broken towards the smaller offered
+load (fewer loads in flight), then LDG before cp.async before TMA.
+
+Infeasible points (shared memory, registers, occupancy) are recorded with
+their status instead of being silently shrunk.
+"""
+from __future__ import annotations
+
+import statistics
+from dataclasses import dataclass, field
+
+from . import (SL_ASC, SL_CPASYNC, SL_LDG, SL_OK, SL_TMA, SL_U32, SLError, config, sl_plan, sl_sweep)
+
+MECH_NAMES = {SL_LDG: "ldg", SL_CPASYNC: "cpasync", SL_TMA: "tma"}
+
+
+@dataclass
+class Point:
+    mech: int
+    k: int = 0            # K (LDG) or D (cp.async)
+    cta: int = 256
+    grid: int = 0
+    stage_bytes: int = 0  # TMA
+    stages: int = 0       # TMA
+    cop: int = 0
+    gbs: list = field(default_factory=list)  # per repeat
+    window_gbs: list = field(default_factory=list)
+    status: int = SL_OK
+    resident: int = 0
+    grid_used: int = 0
+
+    def cfg(self, **kw):
+        if self.mech == SL_TMA:
+            return config(self.mech, cta=self.cta, grid=self.grid, stage_bytes=self.stage_bytes,
+                          stages=self.stages, **kw)
+        return config(self.mech, k=self.k, cta=self.cta, grid=self.grid, cop=self.cop, **kw)
+
+    @property
+    def median(self) -> float:
+        return statistics.median(self.gbs) if self.gbs else 0.0
+
+    @property
+    def offered(self) -> int:
+        """Offered in-flight bytes per CTA (for tie-breaking)."""
+        if self.mech == SL_TMA:
+            return self.stage_bytes * self.stages
+        return self.k * self.cta * 16
+
+    def label(self) -> str:
+        if self.mech == SL_TMA:
+            return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}"
+        return f"{MECH_NAMES[self.mech]} {'K' if self.mech == SL_LDG else 'D'}={self.k} cta={self.cta} cop={self.cop}"
+
+    def as_dict(self) -> dict:
+        d = {"mech": MECH_NAMES[self.mech], "cta": self.cta, "grid": self.grid_used, "status": self.status,
+             "resident_per_sm": self.resident, "gbs_median": round(self.median, 1),
+             "gbs": [round(v, 1) for v in self.gbs]}
+        if self.mech == SL_TMA:
+            d.update(stage_bytes=self.stage_bytes, stages=self.stages)
+        else:
+            d.update(k=self.k, cop=self.cop)
+        return d
+
+
+def default_points(cta: int = 256) -> list[Point]:
+    pts = [Point(SL_LDG, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8, 12, 16)]
+    pts += [Point(SL_LDG, k=k, cta=cta, cop=1) for k in (1, 2, 4, 8)]
+    pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in (1, 2, 4, 8)]
+    pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n)
+            for s in (4096, 16384, 65536) for n in (2, 4, 8) if s * n <= 227 * 1024]
+    return pts
+
+
+def measure(buf, nbytes: int, points: list[Point], dtype: int = SL_U32, repeats: int = 3, warmup: int = 1,
+            sweep_order=SL_ASC, flush_l2: bool = False) -> list[Point]:
+    """Measure every point with sl_sweep (one sweep over all feasible cells)."""
+    feasible = []
+    for p in points:
+        try:
+            r = sl_plan(nbytes, dtype, p.cfg())
+            p.resident = r.resident_per_sm
+            p.grid_used = r.grid
+            feasible.append(p)
+        except SLError as e:
+            p.status = e.status
+    if not feasible:
+        return points
+    rows = sl_sweep(buf, [p.cfg(flush_l2=flush_l2) for p in feasible], nbytes=nbytes, dtype=dtype,
+                    repeats=repeats, warmup=warmup, sweep_order=sweep_order)
+    for p, row in zip(feasible, rows):
+        p.status = next((r.status for r in row if r.status != SL_OK), SL_OK)
+        p.gbs = [nbytes / r.device_ns for r in row if r.status == SL_OK and r.device_ns]
+        p.window_gbs = [nbytes / r.window_ns for r in row if r.status == SL_OK and r.window_ns]
+    return points
+
+
+def choose(points: list[Point], tie_frac: float = 0.005) -> Point:
+    ok = [p for p in points if p.status == SL_OK and p.gbs]
+    if not ok:
+        raise RuntimeError("no feasible measured point")
+    best = max(p.median for p in ok)
+    ties = [p for p in ok if p.median >= best * (1 - tie_frac)]
+    return min(ties, key=lambda p: (p.offered, p.mech))

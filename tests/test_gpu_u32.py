@@ -1,0 +1,213 @@
+"""GPU parity of the uint32 streaming checksum against the CPU oracle, through
+the C ABI: every mechanism and launch shape must give the oracle's checksum
+bit-exactly, and issued loads must equal passes*bytes/16 (zero mismatch)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_15764_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEED = 1
+# several tiles of every shape plus a ragged tail (not a multiple of any tile)
+NBYTES = (1 << 24) + 16 * 1237
+
+
+@pytest.fixture(scope="module")
+def sl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_15764_gb300 as sl
+    sl.load()
+    return sl
+
+
+@pytest.fixture(scope="module")
+def data(sl):
+    """Device buffer filled on the GPU, and the oracle's checksum of the same
+    words generated on the host."""
+    dev = torch.empty(NBYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(dev, seed=SEED)
+    host = workloads.splitmix_u32(SEED, NBYTES // 4)
+    return dev, host, oracle.checksum(host)
+
+
+def _check(sl, dev, nbytes, want, cfg, passes=1):
+    r = sl.sl_run(dev, nbytes=nbytes, dtype=sl.SL_U32, cfg=cfg)
+    assert r.status == 0
+    assert (r.sum_u32, r.xor_u64) == want
+    assert r.issued_loads == oracle.issued_loads(nbytes, passes)
+    return r
+
+
+def test_device_fill_matches_host_generator(sl, data):
+    dev, host, _ = data
+    got = dev.view(torch.int32).cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, host)
+
+
+@pytest.mark.parametrize("k", list(range(1, 17)))
+@pytest.mark.parametrize("order", ["asc", "desc"])
+def test_ldg_every_k(sl, data, k, order):
+    dev, _, want = data
+    _check(sl, dev, NBYTES, want, sl.config("ldg", k=k, cta=256, order=order))
+
+
+@pytest.mark.parametrize("cta", [32, 128, 512, 1024])
+@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("cop", [0, 1, 2])
+def test_ldg_cta_and_cop(sl, data, cta, k, cop):
+    dev, _, want = data
+    _check(sl, dev, NBYTES, want, sl.config("ldg", k=k, cta=cta, cop=cop))
+
+
+@pytest.mark.parametrize("grid", [1, 7, 152, 10007])
+def test_ldg_grids(sl, data, grid):
+    dev, _, want = data
+    r = _check(sl, dev, NBYTES, want, sl.config("ldg", k=4, cta=128, grid=grid))
+    assert r.grid == grid
+
+
+@pytest.mark.parametrize("d", list(range(1, 9)))
+@pytest.mark.parametrize("cta", [128, 256, 1024])
+@pytest.mark.parametrize("order", ["asc", "desc"])
+def test_cpasync_every_depth(sl, data, d, cta, order):
+    dev, _, want = data
+    _check(sl, dev, NBYTES, want, sl.config("cpasync", k=d, cta=cta, order=order))
+
+
+@pytest.mark.parametrize("stage", [4096, 16384, 65536])
+@pytest.mark.parametrize("stages", [2, 3, 4, 8])
+@pytest.mark.parametrize("order", ["asc", "desc"])
+def test_tma_ring(sl, data, stage, stages, order):
+    dev, _, want = data
+    cfg = sl.config("tma", cta=256, stage_bytes=stage, stages=stages, order=order)
+    if stage * stages > 227 * 1024:
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_run(dev, dtype=sl.SL_U32, cfg=cfg)
+        assert e.value.status == sl.SL_ERR_INFEASIBLE
+        return
+    _check(sl, dev, NBYTES, want, cfg)
+
+
+@pytest.mark.parametrize("cta", [32, 128, 992])
+@pytest.mark.parametrize("grid", [1, 3, 0])
+def test_tma_shapes(sl, data, cta, grid):
+    dev, _, want = data
+    _check(sl, dev, NBYTES, want, sl.config("tma", cta=cta, grid=grid, stage_bytes=16384, stages=4))
+
+
+@pytest.mark.parametrize("mech,kw", [("ldg", {"k": 2}), ("ldg", {"k": 13}), ("cpasync", {"k": 3}),
+                                     ("tma", {"stage_bytes": 4096, "stages": 3})])
+@pytest.mark.parametrize("passes", [2, 3])
+def test_passes_closed_form(sl, data, mech, kw, passes):
+    dev, _, (s, x) = data
+    want = ((passes * s) % (1 << 32), x if passes % 2 else 0)
+    _check(sl, dev, NBYTES, want, sl.config(mech, cta=256, passes=passes, **kw), passes=passes)
+
+
+@pytest.mark.parametrize("nvec", [0, 1, 2, 3, 31, 33, 255, 257, 4096 + 5])
+@pytest.mark.parametrize("mech,kw", [("ldg", {"k": 1}), ("ldg", {"k": 16}), ("cpasync", {"k": 8}),
+                                     ("tma", {"stage_bytes": 4096, "stages": 2})])
+def test_small_and_ragged(sl, data, nvec, mech, kw):
+    dev, host, _ = data
+    nbytes = 16 * nvec
+    want = oracle.checksum(host[: nbytes // 4])
+    _check(sl, dev, nbytes, want, sl.config(mech, cta=256, **kw))
+
+
+def test_empty_buffer(sl):
+    r = sl.sl_run(0, nbytes=0, dtype=sl.SL_U32, cfg=sl.config("ldg", k=2))
+    assert (r.sum_u32, r.xor_u64, r.issued_loads, r.grid) == (0, 0, 0, 0)
+
+
+def test_offset_views(sl, data):
+    """A buffer that starts 16 bytes into the allocation (aligned, not at a
+    tile boundary of anything)."""
+    dev, host, _ = data
+    nbytes = NBYTES - 64
+    want = oracle.checksum(host[4: 4 + nbytes // 4])
+    for cfg in [sl.config("ldg", k=4), sl.config("cpasync", k=2), sl.config("tma", stage_bytes=16384, stages=4)]:
+        r = sl.sl_run(dev.data_ptr() + 16, nbytes=nbytes, dtype=sl.SL_U32, cfg=cfg)
+        assert (r.sum_u32, r.xor_u64) == want
+
+
+def test_argument_errors(sl, data):
+    dev, _, _ = data
+    E = sl.SLError
+    cases = [
+        (dict(buf=dev.data_ptr() + 8, nbytes=1024, cfg=sl.config("ldg")), sl.SL_ERR_ALIGN),
+        (dict(buf=dev, nbytes=1000, cfg=sl.config("ldg")), sl.SL_ERR_ALIGN),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", k=0)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", k=17)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", cta=100)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", cta=64)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=9)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stage_bytes=8192)), sl.SL_ERR_INFEASIBLE),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stages=1)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stage_bytes=65536, stages=4)), sl.SL_ERR_INFEASIBLE),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", k=16, cta=1024)), sl.SL_ERR_INFEASIBLE),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", passes=-1)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config(7)), sl.SL_ERR_ARG),
+        (dict(buf=0, nbytes=1024, cfg=sl.config("ldg")), sl.SL_ERR_ARG),
+    ]
+    for kw, code in cases:
+        with pytest.raises(E) as e:
+            sl.sl_run(kw["buf"], nbytes=kw["nbytes"], dtype=sl.SL_U32, cfg=kw["cfg"])
+        assert e.value.status == code, (kw, e.value)
+        assert sl.sl_last_error()
+    with pytest.raises(E) as e:
+        sl.sl_run(dev, nbytes=1024, dtype=9, cfg=sl.config("ldg"))
+    assert e.value.status == sl.SL_ERR_ARG
+    # the context is still fine afterwards
+    r = sl.sl_run(dev, nbytes=1024, dtype=sl.SL_U32, cfg=sl.config("ldg"))
+    assert r.issued_loads == 64
+
+
+def test_sweep_orders_agree(sl, data):
+    dev, _, want = data
+    cells = [sl.config("ldg", k=k) for k in (1, 2, 4, 8)] + [sl.config("tma", stage_bytes=65536, stages=4)]
+    asc = sl.sl_sweep(dev, cells, dtype=sl.SL_U32, repeats=2, warmup=1, sweep_order="asc")
+    desc = sl.sl_sweep(dev, cells, dtype=sl.SL_U32, repeats=2, warmup=1, sweep_order="desc")
+    for rows in (asc, desc):
+        for row in rows[:4]:
+            for r in row:
+                assert r.status == 0 and (r.sum_u32, r.xor_u64) == want and r.device_ns > 0
+        assert all(r.status == sl.SL_ERR_INFEASIBLE for r in rows[4])
+
+
+def test_enqueue_many_on_one_stream(sl, data):
+    dev, _, want = data
+    n = 40
+    rb = sl.RESULT_BYTES
+    out = torch.zeros(rb * n, dtype=torch.uint8, device="cuda")
+    cfgs = [sl.config("ldg", k=1 + i % 16) if i % 3 == 0 else
+            sl.config("cpasync", k=1 + i % 8) if i % 3 == 1 else
+            sl.config("tma", stage_bytes=4096 << (2 * (i % 2)), stages=2 + i % 5) for i in range(n)]
+    for i, c in enumerate(cfgs):
+        sl.sl_enqueue(dev, out[rb * i:], dtype=sl.SL_U32, cfg=c)
+    torch.cuda.synchronize()
+    raw = out.cpu().numpy().tobytes()
+    for i in range(n):
+        r = sl.sl_result.from_buffer_copy(raw[rb * i: rb * (i + 1)])
+        assert (r.sum_u32, r.xor_u64, r.status) == (*want, 0)
+        assert r.issued_loads == NBYTES // 16
+
+
+@pytest.mark.parametrize("mech,kw", [("ldg", {"k": 4}), ("tma", {"stage_bytes": 16384, "stages": 4})])
+def test_run_host_matches(sl, data, mech, kw):
+    _, host, want = data
+    pinned = torch.from_numpy(host.view(np.uint8)).pin_memory()
+    r = sl.sl_run_host(pinned, dtype=sl.SL_U32, cfg=sl.config(mech, **kw))
+    assert (r.sum_u32, r.xor_u64) == want and r.issued_loads == NBYTES // 16
+    # pageable numpy memory works too
+    r = sl.sl_run_host(host, dtype=sl.SL_U32, cfg=sl.config(mech, **kw))
+    assert (r.sum_u32, r.xor_u64) == want
+
+
+def test_device_info(sl):
+    info = sl.sl_device_info()
+    assert info["sm_count"] > 0 and info["l2_bytes"] > 0
+    assert (info["cc_major"], info["cc_minor"]) == (10, 3)
