@@ -215,6 +215,38 @@ int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
                 sl_result* out);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory: code running under a
+ * framework whose own pool allocator owns (nearly) all device memory, code in
+ * a latency-critical loop where cudaMalloc/cudaFree may synchronize the
+ * device, or a plugin or callback whose host contract forbids allocating.
+ * The other entry points allocate their scratch lazily and may grow it.
+ *
+ * sl_run_noalloc runs the LDG mechanism (cfg->mech must be SL_LDG; no L2
+ * flush, no debug flags) like sl_enqueue: asynchronous on cfg->stream, the
+ * result written to the DEVICE pointer dev_out (8-byte aligned), computing
+ * the same checksum, issued-load count and float sum as sl_run.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (per-warp
+ * partials, timestamps, the error word) is one fixed file-scope __device__
+ * array of SL_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the
+ * library until the process exits.  Limits: at most SL_NOALLOC_MAX_CTAS CTAs
+ * and SL_NOALLOC_MAX_WARP_PARTIALS warps (CTAs x cta/32) per call; larger
+ * launches are rejected with SL_ERR_ARG and a message.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * which keeps the previous call's contents (the error word is cleared by each
+ * call): calls whose work overlaps on the GPU (different streams, or other
+ * threads) race and must be serialized by the caller. */
+#define SL_NOALLOC_MAX_CTAS 4096
+#define SL_NOALLOC_MAX_WARP_PARTIALS 32768
+#define SL_NOALLOC_SCRATCH_BYTES (SL_NOALLOC_MAX_WARP_PARTIALS * 32 + SL_NOALLOC_MAX_CTAS * 16 + 256)
+int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+                   sl_result* dev_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -362,6 +362,11 @@ int run_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const 
 
 }  // namespace
 
+namespace sl {
+// Record a failure for sl_last_error() from another translation unit.
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace sl
+
 extern "C" {
 
 const char* sl_last_error(void) { return g_err; }

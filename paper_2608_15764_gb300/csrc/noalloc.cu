@@ -1,0 +1,147 @@
+// noalloc.cu -- sl_run_noalloc: the LDG streaming checksum for callers that
+// cannot allocate device memory.
+//
+// Who needs this: code that runs where a cudaMalloc is not acceptable --
+// inside a framework whose own pool allocator owns (nearly) all device
+// memory, so an allocation behind its back can fail or fragment the pool;
+// in a latency-critical loop, where cudaMalloc/cudaFree may synchronize the
+// device; or in a plugin or callback whose host contract forbids allocating.
+// The regular entry points allocate their scratch lazily (and may grow it,
+// which synchronizes the device), so such callers cannot use them.
+//
+// Here the scratch -- per-warp partials, per-CTA timestamps and the device
+// error word -- lives in one file-scope __device__ array of fixed size
+// (SL_NOALLOC_SCRATCH_BYTES).  Every GPU that loads this library holds that
+// array until the process exits.  Host code never uses the array's name as an
+// address (on the host it is only a stand-in); it asks the runtime for the
+// device address with cudaGetSymbolAddress, once per device, with that device
+// current, and passes that pointer to the kernels.
+#include <cstdint>
+#include <mutex>
+
+#include "sl_internal.h"
+
+namespace {
+
+constexpr uint64_t NA_MAX_PARTS = SL_NOALLOC_MAX_WARP_PARTIALS;
+constexpr uint64_t NA_MAX_CTAS = SL_NOALLOC_MAX_CTAS;
+constexpr uint64_t NA_PARTS_OFF = 0;
+constexpr uint64_t NA_TS_OFF = NA_PARTS_OFF + NA_MAX_PARTS * sizeof(sl::WarpPartial);
+constexpr uint64_t NA_ERR_OFF = NA_TS_OFF + 2 * NA_MAX_CTAS * sizeof(uint64_t);
+constexpr uint64_t NA_BYTES = NA_ERR_OFF + 256;
+static_assert(NA_BYTES == SL_NOALLOC_SCRATCH_BYTES, "scratch layout");
+
+// The fixed scratch.  Shared by every sl_run_noalloc call on a device; it
+// keeps the previous call's contents, so the error word is cleared before
+// each launch (partials and timestamps are fully rewritten by the kernel).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SL_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on device `dev` (which must be
+// current), looked up once per device.
+int scratch_for(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> g(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return sl::set_error(SL_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch failed");
+        }
+        g_na_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_na_ptr[dev];
+    return SL_OK;
+}
+
+int na_fail(int code, const char* msg) { return sl::set_error(code, msg); }
+
+}  // namespace
+
+extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+                              sl_result* dev_out) {
+    if (!cfg) return na_fail(SL_ERR_ARG, "cfg is NULL");
+    if (cfg->mech != SL_LDG) return na_fail(SL_ERR_ARG, "sl_run_noalloc supports the LDG mechanism only");
+    if (cfg->flush_l2) return na_fail(SL_ERR_ARG, "sl_run_noalloc cannot flush L2 (the flush buffer is allocated)");
+    if (cfg->debug_flags) return na_fail(SL_ERR_ARG, "sl_run_noalloc takes no debug flags");
+    if (dtype < SL_U32 || dtype > SL_FP8_E4M3) return na_fail(SL_ERR_ARG, "bad dtype");
+    if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u)) return na_fail(SL_ERR_ARG, "dev_out NULL or not 8-byte aligned");
+    if ((bytes & 15u) != 0) return na_fail(SL_ERR_ALIGN, "bytes not a multiple of 16");
+    if (bytes > 0 && !dev_buf) return na_fail(SL_ERR_ARG, "buffer is NULL");
+    if ((reinterpret_cast<uintptr_t>(dev_buf) & 15u) != 0) return na_fail(SL_ERR_ALIGN, "buffer not 16-byte aligned");
+    if (cfg->passes < 0) return na_fail(SL_ERR_ARG, "passes < 0");
+    if (cfg->order != SL_ASC && cfg->order != SL_DESC) return na_fail(SL_ERR_ARG, "bad order");
+    if (cfg->k < 1 || cfg->k > SL_MAX_K) return na_fail(SL_ERR_ARG, "K not in 1..16");
+    const int cta = cfg->cta;
+    const void* fn = sl::ldg_kernel(dtype, cfg->k, cta, cfg->cop);
+    if (!fn) return na_fail(SL_ERR_ARG, "no LDG kernel for this dtype / K / cta / cop");
+
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
+        (void)cudaGetLastError();
+        return na_fail(SL_ERR_NODEV, "no usable CUDA device");
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return na_fail(SL_ERR_CUDA, "cudaFuncGetAttributes failed");
+    }
+    if (fa.localSizeBytes > 0 || fa.numRegs < 4 * cfg->k + 16)
+        return na_fail(SL_ERR_INFEASIBLE, "this LDG kernel cannot keep K loads in registers at this cta");
+    int resident = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, fn, cta, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return na_fail(SL_ERR_CUDA, "occupancy / SM-count query failed");
+    }
+    if (resident < 1) return na_fail(SL_ERR_INFEASIBLE, "zero occupancy");
+    const uint64_t grid = cfg->grid > 0 ? static_cast<uint64_t>(cfg->grid)
+                                        : static_cast<uint64_t>(resident < 4 ? resident : 4) * sms;
+    const uint64_t nparts = grid * static_cast<uint64_t>(cta / 32);
+    if (grid > NA_MAX_CTAS || nparts > NA_MAX_PARTS)
+        return na_fail(SL_ERR_ARG, "launch exceeds the fixed scratch: at most SL_NOALLOC_MAX_CTAS CTAs and "
+                                   "SL_NOALLOC_MAX_WARP_PARTIALS warps (CTAs x cta/32)");
+
+    unsigned char* base = nullptr;
+    int rc = scratch_for(dev, &base);
+    if (rc) return rc;
+    sl::WarpPartial* parts = reinterpret_cast<sl::WarpPartial*>(base + NA_PARTS_OFF);
+    uint64_t* tstamp = reinterpret_cast<uint64_t*>(base + NA_TS_OFF);
+    uint32_t* err = reinterpret_cast<uint32_t*>(base + NA_ERR_OFF);
+    cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+
+    if (cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return na_fail(SL_ERR_CUDA, "clearing the error word failed");
+    }
+    const uint64_t nvec = bytes / 16;
+    const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
+    const uint64_t launched = nvec == 0 ? 0 : grid;
+    if (launched) {
+        sl::KArgs a{};
+        const uint64_t tile_vec = static_cast<uint64_t>(cta) * cfg->k;
+        a.buf = dev_buf;
+        a.nvec = nvec;
+        a.ntiles = (nvec + tile_vec - 1) / tile_vec;
+        a.total = a.ntiles * passes;
+        a.tile_vec = static_cast<uint32_t>(tile_vec);
+        a.desc = cfg->order == SL_DESC ? 1 : 0;
+        a.parts = parts;
+        a.tstamp = tstamp;
+        a.err = err;
+        a.timeout_ns = 2000000000ull;
+        void* args[] = {&a};
+        if (cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(cta), args, 0, s) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return na_fail(SL_ERR_CUDA, "kernel launch failed");
+        }
+    }
+    if (sl::launch_combine(parts, launched * (cta / 32), tstamp, launched, err, dev_out, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return na_fail(SL_ERR_CUDA, "combine launch failed");
+    }
+    return SL_OK;
+}

@@ -48,6 +48,9 @@ const void* ldg_kernel(int dtype, int k, int cta, int cop);
 const void* cpasync_kernel(int dtype, int d);
 const void* tma_kernel(int dtype);
 
+// Record a failure message for sl_last_error(); returns code (api.cu).
+int set_error(int code, const char* msg);
+
 // Utility launches (k_util.cu); asynchronous on `s`.
 cudaError_t launch_fill_splitmix64(void* buf, uint64_t nvec, uint64_t seed, int sms, cudaStream_t s);
 cudaError_t launch_flush(void* buf, uint64_t nvec, int sms, cudaStream_t s);
