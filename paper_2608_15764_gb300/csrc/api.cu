@@ -179,7 +179,7 @@ struct Plan {
     int64_t grid = 0;         // CTAs (0: nothing to launch)
     size_t smem = 0;          // dynamic shared memory
     int resident = 0;         // occupancy-API CTAs per SM
-    uint64_t warps = 0;       // folding warps per CTA
+    uint64_t warps = 0;       // folding warps per CTA (each CTA writes one partial)
     KArgs args{};
 };
 
@@ -293,6 +293,12 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (grid <= 0) grid = static_cast<int64_t>(std::min(4, p->resident)) * c->info.sm_count;
     if (grid > MAX_GRID) return fail(SL_ERR_ARG, "grid %lld > %lld", (long long)grid, (long long)MAX_GRID);
     p->grid = nvec == 0 ? 0 : grid;
+    // The kernels count tiles and per-thread loads in 32 bits.
+    const uint64_t total = ntiles * passes;
+    const uint64_t per_thread = ((total + grid - 1) / grid) * ((tile_vec + cta - 1) / cta);
+    if (total + static_cast<uint64_t>(grid) >= (1ull << 32) || per_thread >= (1ull << 32))
+        return fail(SL_ERR_ARG, "passes x tiles too large for one launch (%llu tiles); lower passes",
+                    (unsigned long long)total);
     KArgs& a = p->args;
     a.buf = buf;
     a.nvec = nvec;
@@ -328,7 +334,7 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
     int rc = make_plan(c, buf, bytes, dtype, cfg, &p);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
-    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid) * p.warps, static_cast<uint64_t>(p.grid));
+    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid), static_cast<uint64_t>(p.grid));
     if (rc) return rc;
     p.args.parts = c->parts;
     p.args.tstamp = c->tstamp;
@@ -338,7 +344,7 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
     rc = launch(p, s);
     if (rc) return rc;
     if (events) CUDA_TRY(cudaEventRecord(c->ev1, s));
-    CUDA_TRY(sl::launch_combine(c->parts, static_cast<uint64_t>(p.grid) * p.warps, c->tstamp,
+    CUDA_TRY(sl::launch_combine(c->parts, static_cast<uint64_t>(p.grid), c->tstamp,
                                 static_cast<uint64_t>(p.grid), c->err, dev_out, s));
     if (plan_out) *plan_out = p;
     return SL_OK;
@@ -491,7 +497,7 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
     Plan p;
     rc = make_plan(c, c->stage[0], chunk, dtype, cfg, &p);
     if (rc) return rc;
-    const uint64_t per_parts = static_cast<uint64_t>(p.grid) * p.warps;
+    const uint64_t per_parts = static_cast<uint64_t>(p.grid);  // one partial per CTA
     rc = ensure_scratch(c, per_parts * nchunks, static_cast<uint64_t>(p.grid) * nchunks);
     if (rc) return rc;
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);

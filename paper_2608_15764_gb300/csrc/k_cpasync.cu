@@ -27,15 +27,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 struct ChunkCursor {
     TileCursor c;
     uint32_t k;
-    __device__ __forceinline__ void start(uint64_t ntiles) { c.start(ntiles); k = 0; }
+    __device__ __forceinline__ void start(uint32_t ntiles) { c.start(ntiles); k = 0; }
     template <int D>
-    __device__ __forceinline__ void next(uint64_t ntiles) {
+    __device__ __forceinline__ void next(uint32_t ntiles) {
         if (++k == D) { k = 0; c.next(ntiles); }
     }
     // vector index of this thread's chunk, or ~0 when past the end
-    __device__ __forceinline__ uint64_t vec(const KArgs& a, uint32_t cta) const {
-        if (c.it >= a.total) return ~0ull;
-        const uint64_t idx = c.tile(a) * a.tile_vec + static_cast<uint64_t>(k) * cta + threadIdx.x;
+    __device__ __forceinline__ uint64_t vec(const KArgs& a, uint32_t total, uint32_t cta) const {
+        if (c.it >= total) return ~0ull;
+        const uint64_t idx = static_cast<uint64_t>(c.tile(a)) * a.tile_vec + k * cta + threadIdx.x;
         return idx < a.nvec ? idx : ~0ull;
     }
 };
@@ -43,45 +43,45 @@ struct ChunkCursor {
 template <int D, int DT>
 __global__ void __launch_bounds__(1024) k_cpasync(const KArgs a) {
     extern __shared__ __align__(16) uint4 ring[];  // [D][cta]
-    const uint64_t t0 = gtimer();
+    cta_start(a);
     const uint32_t cta = blockDim.x;
+    const uint32_t ntiles = static_cast<uint32_t>(a.ntiles);
+    const uint32_t total = static_cast<uint32_t>(a.total);
     const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
     const uint32_t my_slot0 = smem_addr(ring + threadIdx.x);
     const uint32_t slot_stride = cta * 16u;
     Acc<DT> acc;
     ChunkCursor ic, cc;  // issue and consume cursors
-    ic.start(a.ntiles);
-    cc.start(a.ntiles);
+    ic.start(ntiles);
+    cc.start(ntiles);
     uint32_t islot = 0, cslot = 0;
 
 #pragma unroll
     for (int g = 0; g < D - 1; ++g) {
-        const uint64_t idx = ic.vec(a, cta);
+        const uint64_t idx = ic.vec(a, total, cta);
         if (idx != ~0ull) cp_async16(my_slot0 + islot * slot_stride, buf + idx);
         cp_async_commit();
-        ic.next<D>(a.ntiles);
+        ic.next<D>(ntiles);
         islot = (islot + 1 == D) ? 0 : islot + 1;
     }
 #pragma unroll 1
-    while (cc.c.it < a.total) {
-        const uint64_t idx = ic.vec(a, cta);
+    while (cc.c.it < total) {
+        const uint64_t idx = ic.vec(a, total, cta);
         if (idx != ~0ull) cp_async16(my_slot0 + islot * slot_stride, buf + idx);
         cp_async_commit();
-        ic.next<D>(a.ntiles);
+        ic.next<D>(ntiles);
         islot = (islot + 1 == D) ? 0 : islot + 1;
 
         cp_async_wait<D - 1>();
-        if (cc.vec(a, cta) != ~0ull) {
+        if (cc.vec(a, total, cta) != ~0ull) {
             acc.fold(lds16(my_slot0 + cslot * slot_stride));
             acc.n += 1;
         }
-        cc.next<D>(a.ntiles);
+        cc.next<D>(ntiles);
         cslot = (cslot + 1 == D) ? 0 : cslot + 1;
     }
     cp_async_wait<0>();
-    const uint32_t nwarps = cta >> 5;
-    warp_store<DT>(acc, a.parts + static_cast<uint64_t>(blockIdx.x) * nwarps + (threadIdx.x >> 5));
-    cta_stamp(a, t0);
+    cta_finish<DT>(acc, true, threadIdx.x >> 5, cta >> 5, a);
 }
 
 template <int DT>

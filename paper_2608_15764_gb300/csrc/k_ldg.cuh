@@ -24,18 +24,19 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
     // registers; configurations whose kernel would spill are rejected on the
     // host (local memory > 0), as the paper requires zero spills (§3).
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
-    const uint64_t t0 = gtimer();
+    cta_start(a);
     const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
-    const uint64_t ntiles = a.ntiles;
-    const bool last_full = (a.nvec == ntiles * TILE);
+    const uint32_t ntiles = static_cast<uint32_t>(a.ntiles);
+    const uint32_t total = static_cast<uint32_t>(a.total);
+    const bool last_full = (a.nvec == static_cast<uint64_t>(ntiles) * TILE);
     Acc<DT> acc;
     uint32_t full_iters = 0;
     TileCursor c;
     c.start(ntiles);
 #pragma unroll 1
-    for (; c.it < a.total; c.next(ntiles)) {
-        const uint64_t tile = c.tile(a);
-        const uint4* p = buf + tile * TILE + threadIdx.x;
+    for (; c.it < total; c.next(ntiles)) {
+        const uint32_t tile = c.tile(a);
+        const uint4* p = buf + static_cast<uint64_t>(tile) * TILE + threadIdx.x;
         uint4 v[K];
         if (last_full || tile + 1 < ntiles) {
             // K independent loads issued back to back, then consumed.
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
             ++full_iters;
         } else {
             // Ragged last tile: only vectors below nvec are loaded.
-            const uint32_t rem = static_cast<uint32_t>(a.nvec - tile * TILE);
+            const uint32_t rem = static_cast<uint32_t>(a.nvec - static_cast<uint64_t>(tile) * TILE);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 if (threadIdx.x + k * CTA < rem) v[k] = ldg16<COP>(p + k * CTA);
@@ -61,9 +62,8 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
             }
         }
     }
-    acc.n += static_cast<uint64_t>(full_iters) * K;
-    warp_store<DT>(acc, a.parts + static_cast<uint64_t>(blockIdx.x) * (CTA / 32) + (threadIdx.x >> 5));
-    cta_stamp(a, t0);
+    acc.n += full_iters * K;
+    cta_finish<DT>(acc, true, threadIdx.x >> 5, CTA / 32, a);
 }
 
 }  // namespace sl

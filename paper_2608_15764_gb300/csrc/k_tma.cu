@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     __shared__ __align__(8) uint64_t empty[SL_MAX_STAGES];
     __shared__ volatile int abort_flag;
 
-    const uint64_t t0 = gtimer();
+    cta_start(a);
     const uint32_t nst = static_cast<uint32_t>(a.nst);
+    const uint32_t ntiles = static_cast<uint32_t>(a.ntiles);
+    const uint32_t total = static_cast<uint32_t>(a.total);
     const uint32_t stage_bytes = a.tile_vec * 16u;
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t ncw = (blockDim.x >> 5) - 1;  // consumer warps
@@ -108,13 +110,13 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
             uint32_t armed = 0;     // bit s: stage s has had a copy issued
             uint32_t last_par = 0;  // bit s: parity of the round of stage s's last copy
             TileCursor c;
-            c.start(a.ntiles);
+            c.start(ntiles);
             uint32_t s = 0, r = 0;  // stage and round of chunk i = r*nst + s
-            for (uint64_t i = 0; c.it < a.total; c.next(a.ntiles), ++i) {
+            for (uint32_t i = 0; c.it < total; c.next(ntiles), ++i) {
                 if (r > 0 && !bounded_wait(empty0 + 8 * s, (r - 1) & 1u, a, &abort_flag, true,
                                            DEV_ERR_TIMEOUT_EMPTY))
                     break;
-                const uint64_t off = c.tile(a) * stage_bytes;
+                const uint64_t off = static_cast<uint64_t>(c.tile(a)) * stage_bytes;
                 const uint64_t left = bytes - off;
                 const uint32_t len = left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes;
                 if (!((a.debug & SL_DEBUG_TMA_SKIP_STAGE) && i == 1)) {  // debug: leave chunk 1 unarmed
@@ -139,12 +141,12 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
         // ---- consumers ----
         const uint32_t ct = threadIdx.x - 32, nct = ncw * 32;
         TileCursor c;
-        c.start(a.ntiles);
+        c.start(ntiles);
         uint32_t s = 0, r = 0;
-        for (; c.it < a.total; c.next(a.ntiles)) {
+        for (; c.it < total; c.next(ntiles)) {
             const bool got = bounded_wait(full0 + 8 * s, r & 1u, a, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
             if (!__all_sync(FULL_MASK, got)) break;  // warp-uniform exit
-            const uint64_t off = c.tile(a) * stage_bytes;
+            const uint64_t off = static_cast<uint64_t>(c.tile(a)) * stage_bytes;
             const uint64_t left = bytes - off;
             const uint32_t nv = (left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes) >> 4;
             const uint32_t base = ring0 + s * stage_bytes;
@@ -157,9 +159,9 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
             if (lane == 0) mbar_arrive(empty0 + 8 * s);
             if (++s == nst) { s = 0; ++r; }
         }
-        warp_store<DT>(acc, a.parts + static_cast<uint64_t>(blockIdx.x) * ncw + (warp - 1));
     }
-    cta_stamp(a, t0);
+    // consumer warps fold (all lanes left the ring together); warp 0 does not
+    cta_finish<DT>(acc, warp != 0, warp - 1, ncw, a);
 }
 
 const void* tma_kernel(int dtype) {

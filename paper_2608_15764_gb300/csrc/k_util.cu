@@ -38,12 +38,12 @@ __global__ void __launch_bounds__(256) k_flush(uint4* __restrict__ buf, uint64_t
         buf[j] = make_uint4(tag, static_cast<uint32_t>(j), 0u, 0u);
 }
 
-// Final combine of per-warp partials into one sl_result.  One CTA of
+// Final combine of per-CTA partials into one sl_result.  One CTA of
 // COMBINE_THREADS threads; thread i folds partials i, i+T, ... in index order,
 // then a fixed shared-memory tree merges the threads, so the FP64 float sum
 // has a fixed order (deterministic for a given launch shape).  Integer parts
 // combine exactly.  The device error word is reported in status and cleared.
-constexpr int COMBINE_THREADS = 256;
+constexpr int COMBINE_THREADS = 512;
 
 __global__ void __launch_bounds__(COMBINE_THREADS) k_combine(const WarpPartial* __restrict__ parts,
                                                             uint64_t nparts,

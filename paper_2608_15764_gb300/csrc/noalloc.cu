@@ -105,6 +105,12 @@ extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype
         return na_fail(SL_ERR_ARG, "launch exceeds the fixed scratch: at most SL_NOALLOC_MAX_CTAS CTAs and "
                                    "SL_NOALLOC_MAX_WARP_PARTIALS warps (CTAs x cta/32)");
 
+    {
+        const uint64_t tv = static_cast<uint64_t>(cta) * cfg->k;
+        const uint64_t tot = (bytes / 16 + tv - 1) / tv * (cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes));
+        if (tot + grid >= (1ull << 32) || (tot + grid - 1) / grid * cfg->k >= (1ull << 32))
+            return na_fail(SL_ERR_ARG, "passes x tiles too large for one launch; lower passes");
+    }
     unsigned char* base = nullptr;
     int rc = scratch_for(dev, &base);
     if (rc) return rc;
@@ -139,7 +145,7 @@ extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype
             return na_fail(SL_ERR_CUDA, "kernel launch failed");
         }
     }
-    if (sl::launch_combine(parts, launched * (cta / 32), tstamp, launched, err, dev_out, s) != cudaSuccess) {
+    if (sl::launch_combine(parts, launched, tstamp, launched, err, dev_out, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return na_fail(SL_ERR_CUDA, "combine launch failed");
     }

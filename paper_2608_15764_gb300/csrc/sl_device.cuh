@@ -118,7 +118,7 @@ __device__ __forceinline__ float vec_sum(const uint4& v) {
 template <int DT>
 struct Acc {
     uint32_t s = 0, xl = 0, xh = 0;
-    uint64_t n = 0;
+    uint32_t n = 0;  // 16-byte loads folded by this thread (the host keeps it below 2^32)
     float ks = 0.0f, kc = 0.0f;
 
     __device__ __forceinline__ void fold(const uint4& v) {
@@ -142,66 +142,111 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = (a - (s - bb)) + (b - bb);
 }
 
-// Reduce the warp's accumulators (shuffle butterfly; float pairs combined as
-// double-float with TwoSum) and let lane 0 store the warp partial.
+// Double-float add of two partials' float parts (TwoSum, then renormalise).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float ohi, float olo) {
+    float sh, se;
+    two_sum(hi, ohi, sh, se);
+    se += lo + olo;
+    hi = sh + se;
+    lo = se - (hi - sh);
+}
+
+// Shuffle-butterfly reduction of one partial per lane: every lane ends with
+// the warp total (integer parts exact; float pairs combined as double-float
+// with TwoSum, in the butterfly's fixed order).
 template <int DT>
-__device__ __forceinline__ void warp_store(const Acc<DT>& a, WarpPartial* dst) {
-    uint32_t s = a.s, xl = a.xl, xh = a.xh;
-    uint64_t n = a.n;
-    float hi = a.ks, lo = -a.kc;
+__device__ __forceinline__ void warp_merge(uint32_t& s, uint64_t& x, uint64_t& n, float& hi, float& lo) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(FULL_MASK, s, o);
-        xl ^= __shfl_xor_sync(FULL_MASK, xl, o);
-        xh ^= __shfl_xor_sync(FULL_MASK, xh, o);
+        x ^= __shfl_xor_sync(FULL_MASK, x, o);
         n += __shfl_xor_sync(FULL_MASK, n, o);
         if constexpr (DT != SL_U32) {
             const float ohi = __shfl_xor_sync(FULL_MASK, hi, o);
             const float olo = __shfl_xor_sync(FULL_MASK, lo, o);
-            float sh, se;
-            two_sum(hi, ohi, sh, se);
-            se += lo + olo;
-            hi = sh + se;
-            lo = se - (hi - sh);
+            df_add(hi, lo, ohi, olo);
         }
     }
-    if ((threadIdx.x & 31) == 0) {
-        WarpPartial p;
-        p.sum = s;
-        p.pad = 0;
-        p.xr = (static_cast<uint64_t>(xh) << 32) | xl;
-        p.issued = n;
-        p.hi = hi;
-        p.lo = lo;
-        *dst = p;
+}
+
+// End of a streaming kernel: every folding warp (all 32 lanes present)
+// reduces its accumulators and lane 0 puts the warp partial in shared memory;
+// after a CTA barrier warp 0 merges the warp partials (butterfly, fixed
+// order) into the CTA's partial a.parts[blockIdx.x], and thread 0 stores the
+// CTA's start/end %globaltimer stamps.  `fw` is this warp's index among the
+// nfw (<= 32) folding warps.
+template <int DT>
+__device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint32_t fw, uint32_t nfw,
+                                           const KArgs& a) {
+    __shared__ WarpPartial sp[32];
+    const uint32_t lane = threadIdx.x & 31;
+    if (folds) {
+        uint32_t s = acc.s;
+        uint64_t x = (static_cast<uint64_t>(acc.xh) << 32) | acc.xl, n = acc.n;
+        float hi = acc.ks, lo = -acc.kc;
+        warp_merge<DT>(s, x, n, hi, lo);
+        if (lane == 0) {
+            WarpPartial p;
+            p.sum = s;
+            p.pad = 0;
+            p.xr = x;
+            p.issued = n;
+            p.hi = hi;
+            p.lo = lo;
+            sp[fw] = p;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t s = 0;
+        uint64_t x = 0, n = 0;
+        float hi = 0.0f, lo = 0.0f;
+        if (lane < nfw) {
+            const WarpPartial p = sp[lane];
+            s = p.sum;
+            x = p.xr;
+            n = p.issued;
+            hi = p.hi;
+            lo = p.lo;
+        }
+        warp_merge<DT>(s, x, n, hi, lo);
+        if (lane == 0) {
+            WarpPartial p;
+            p.sum = s;
+            p.pad = 0;
+            p.xr = x;
+            p.issued = n;
+            p.hi = hi;
+            p.lo = lo;
+            a.parts[blockIdx.x] = p;
+            a.tstamp[2 * blockIdx.x + 1] = gtimer();
+        }
     }
 }
 
 // Tile cursor over the grid-stride sequence it = blockIdx.x, +gridDim.x, ...
-// tm = it mod ntiles (the pass-local tile), tracked without division.
+// tm = it mod ntiles (the pass-local tile), tracked without division.  32-bit:
+// the host keeps total tiles + grid below 2^32.
 struct TileCursor {
-    uint64_t it, tm;
-    __device__ __forceinline__ void start(uint64_t ntiles) {
+    uint32_t it, tm;
+    __device__ __forceinline__ void start(uint32_t ntiles) {
         it = blockIdx.x;
         tm = blockIdx.x % ntiles;
     }
-    __device__ __forceinline__ void next(uint64_t ntiles) {
+    __device__ __forceinline__ void next(uint32_t ntiles) {
         it += gridDim.x;
         tm += gridDim.x;
         while (tm >= ntiles) tm -= ntiles;
     }
-    __device__ __forceinline__ uint64_t tile(const KArgs& a) const {
-        return a.desc ? (a.ntiles - 1 - tm) : tm;
+    __device__ __forceinline__ uint32_t tile(const KArgs& a) const {
+        return a.desc ? (static_cast<uint32_t>(a.ntiles) - 1 - tm) : tm;
     }
 };
 
-// Store the CTA's start/end %globaltimer stamps (after every thread is done).
-__device__ __forceinline__ void cta_stamp(const KArgs& a, uint64_t t0) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        a.tstamp[2 * blockIdx.x] = t0;
-        a.tstamp[2 * blockIdx.x + 1] = gtimer();
-    }
+// Start of a streaming kernel: thread 0 stores the CTA's start %globaltimer
+// stamp (no register holds it through the kernel).
+__device__ __forceinline__ void cta_start(const KArgs& a) {
+    if (threadIdx.x == 0) a.tstamp[2 * blockIdx.x] = gtimer();
 }
 
 }  // namespace sl

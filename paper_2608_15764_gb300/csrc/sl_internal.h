@@ -9,8 +9,8 @@
 
 namespace sl {
 
-// One warp's folded contribution.  The final combine adds sum (mod 2^32),
-// XORs xr, adds issued, and adds (double)hi + (double)lo in FP64.
+// One CTA's (or warp's) folded contribution.  The final combine adds sum
+// (mod 2^32), XORs xr, adds issued, and adds (double)hi + (double)lo in FP64.
 struct __align__(16) WarpPartial {
     uint32_t sum;
     uint32_t pad;
@@ -32,7 +32,7 @@ struct KArgs {
     int32_t desc;           // 1: walk tiles from the last one downward
     int32_t nst;            // TMA: ring stages
     int32_t debug;          // SL_DEBUG_* flags
-    WarpPartial* parts;     // [grid * folding warps per CTA]
+    WarpPartial* parts;     // [grid]: one partial per CTA
     uint64_t* tstamp;       // [2 * grid]: %globaltimer at CTA start / end
     uint32_t* err;          // device error word (0 = fine)
     uint64_t timeout_ns;    // bound of any single device wait

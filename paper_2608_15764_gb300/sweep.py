@@ -1,0 +1,225 @@
+"""Collection harness: the paper's sweeps on GB300, one JSONL row per cell.
+
+Paper §3 "Fixed-work control": every K sweep runs ascending and reversed, with
+total issued logical loads matched across K (here exactly bytes/16 per pass).
+§3 "Hardware counters": the warm-up launch is excluded.  §3 "Timing,
+residency, statistics": the unit is the launch, per-cell medians with
+min-max, and a residency screen flags any HBM cell above the datasheet.
+
+Configurations (buffers of uint32 words from splitmix64(seed=1), filled on the
+GPU and checked against the first cell's checksum):
+
+  c1   256 MiB; LDG K in {1,2,4,8}; 256 threads; grid 4 x SMs.
+  c2   4 GiB; LDG K in {1,2,3,4,6,8,12,16} x CTA {128,256,512} x resident
+       CTAs per SM r = 1..8 (grid = r x SMs; a cell is infeasible when the
+       occupancy API allows fewer than r) x sweep order {asc, desc}.
+  c3   4 GiB; same bytes through LDG K 1..16, cp.async D 1..8 and TMA
+       stage {4,16,64} KiB x stages 2..8 (cells over the shared-memory limit
+       are recorded as infeasible).
+  c4   allocations 512 MiB, 1, 2, 4, 8, 16, 20 GiB; LDG K in {1,2,4,8,16}.
+  ilp  one CTA of one warp (32 threads) on a 32 MiB buffer: time versus K
+       (LDG) and D (cp.async).  With all K loads in flight, a lone warp is
+       latency-bound and its time falls about K-fold at fixed work.
+  primary  the paper's primary cell shape (§4.2: one CTA of 32 warps per SM,
+       .cg, 16-byte loads), K in {1,2,4,8}, on 4 GiB.
+  ncu  a small case for counter captures (1 GiB, one launch per cell, no
+       warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), cp.async D=8, TMA
+       16 KiB x 2 stages.
+
+    python -m paper_2608_15764_gb300.sweep --config c2 --out runs.jsonl [--repeats 10]
+
+A rerun with the same --out skips cells already recorded (resume after an
+interrupted run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import time
+
+DATASHEET_GBS = 8000.0
+
+
+def decline(bw_k2: float, bw_k8: float) -> float:
+    """Endpoint change from K=2 to K=8 in percent (paper §4.2 tables: negative
+    for a decline)."""
+    return 100.0 * (bw_k8 - bw_k2) / bw_k2
+
+
+def _cells(config: str, sms: int):
+    """Yield (cell_key, cell dict) in ascending order."""
+    if config == "c1":
+        for k in (1, 2, 4, 8):
+            yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=0.25)
+    elif config == "c2":
+        for cta in (128, 256, 512):
+            for r in range(1, 9):
+                for k in (1, 2, 3, 4, 6, 8, 12, 16):
+                    yield dict(mech="ldg", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
+    elif config == "c3":
+        for k in range(1, 17):
+            yield dict(mech="ldg", k=k, cta=256, grid=0, gib=4)
+        for d in range(1, 9):
+            yield dict(mech="cpasync", k=d, cta=256, grid=0, gib=4)
+        for sb in (4096, 16384, 65536):
+            for n in range(2, 9):
+                yield dict(mech="tma", stage_bytes=sb, stages=n, cta=256, grid=0, gib=4)
+    elif config == "c4":
+        for gib in (0.5, 1, 2, 4, 8, 16, 20):
+            for k in (1, 2, 4, 8, 16):
+                yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
+    elif config == "ilp":
+        for k in (1, 2, 4, 8, 16):
+            yield dict(mech="ldg", k=k, cta=32, grid=1, gib=1 / 32)
+        for d in (1, 2, 4, 8):
+            yield dict(mech="cpasync", k=d, cta=32, grid=1, gib=1 / 32)
+    elif config == "primary":
+        for k in (1, 2, 4, 8):
+            yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=4)
+    elif config == "ncu":
+        yield dict(mech="ldg", k=2, cta=256, grid=4 * sms, gib=1)
+        yield dict(mech="ldg", k=8, cta=256, grid=4 * sms, gib=1)
+        yield dict(mech="cpasync", k=8, cta=256, grid=0, gib=1)
+        yield dict(mech="tma", stage_bytes=16384, stages=2, cta=256, grid=0, gib=1)
+    else:
+        raise ValueError(config)
+
+
+def _key(cell: dict, order: str) -> str:
+    return json.dumps({**cell, "order": order}, sort_keys=True)
+
+
+def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"), verbose: bool = True,
+        warmup: int = 1):
+    import torch
+
+    import paper_2608_15764_gb300 as sl
+
+    sl.load()
+    info = sl.sl_device_info()
+    sms = info["sm_count"]
+    done = set()
+    if out and os.path.exists(out):
+        for line in open(out):
+            try:
+                row = json.loads(line)
+            except ValueError:
+                continue
+            if row.get("config") == config and "key" in row:
+                done.add(row["key"])
+    cells = list(_cells(config, sms))
+    rows = []
+    by_size = {}
+    for c in cells:
+        by_size.setdefault(c["gib"], []).append(c)
+    for gib, group in by_size.items():
+        nbytes = int(gib * (1 << 30)) // 16 * 16
+        buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        sl.sl_fill_splitmix64(buf, seed=1)
+        torch.cuda.synchronize()
+        ref = None
+        for order in orders:
+            todo = [c for c in group if _key(c, order) not in done]
+            if not todo:
+                continue
+            seq = todo if order == "asc" else list(reversed(todo))
+            cfgs, keep = [], []
+            for c in seq:
+                kw = dict(cta=c["cta"], grid=c["grid"])
+                if c["mech"] == "tma":
+                    cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
+                else:
+                    cfg = sl.config(c["mech"], k=c["k"], **kw)
+                status, resident = 0, 0
+                try:
+                    plan = sl.sl_plan(nbytes, sl.SL_U32, cfg)
+                    resident = plan.resident_per_sm
+                    if c.get("resident_req") and resident < c["resident_req"]:
+                        status = sl.SL_ERR_INFEASIBLE
+                except sl.SLError as e:
+                    status = e.status
+                row = {"config": config, "key": _key(c, order), "order": order, "bytes": nbytes, **c,
+                       "status": status, "resident_per_sm": resident}
+                if status:
+                    rows.append(row)
+                    _emit(out, row, verbose)
+                    continue
+                cfgs.append(cfg)
+                keep.append(row)
+            if not cfgs:
+                continue
+            # one sweep call per order: the cells run back to back in `seq` order
+            res = sl.sl_sweep(buf, cfgs, dtype=sl.SL_U32, repeats=repeats, warmup=warmup, sweep_order="asc")
+            for row, rr in zip(keep, res):
+                ok = [r for r in rr if r.status == 0]
+                gbs = [nbytes / r.device_ns for r in ok if r.device_ns]
+                wgbs = [nbytes / r.window_ns for r in ok if r.window_ns]
+                cks = {(r.sum_u32, r.xor_u64) for r in ok}
+                if ref is None and cks:
+                    ref = next(iter(cks))
+                row.update(
+                    status=0 if len(ok) == len(rr) else rr[0].status,
+                    grid_used=rr[0].grid,
+                    gbs_median=round(statistics.median(gbs), 2) if gbs else None,
+                    gbs_min=round(min(gbs), 2) if gbs else None,
+                    gbs_max=round(max(gbs), 2) if gbs else None,
+                    gbs=[round(v, 2) for v in gbs],
+                    window_gbs_median=round(statistics.median(wgbs), 2) if wgbs else None,
+                    issued_ok=all(r.issued_loads == nbytes // 16 for r in ok),
+                    checksum_ok=(cks == {ref}),
+                    above_datasheet=bool(gbs and max(gbs) > DATASHEET_GBS),
+                    frac_of_datasheet=round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,
+                )
+                rows.append(row)
+                _emit(out, row, verbose)
+        del buf
+        torch.cuda.empty_cache()
+    return rows
+
+
+def _emit(out, row, verbose):
+    if out:
+        with open(out, "a") as f:
+            f.write(json.dumps(row) + "\n")
+    if verbose:
+        c = {k: row.get(k) for k in ("mech", "k", "stage_bytes", "stages", "cta", "grid", "gib", "order")}
+        print(json.dumps({**{k: v for k, v in c.items() if v is not None}, "status": row["status"],
+                          "gbs": row.get("gbs_median"), "res": row.get("resident_per_sm")}), flush=True)
+
+
+def summarize(rows):
+    """K=2 -> K=8 endpoint change per (config group, order) where both exist."""
+    out = []
+    groups = {}
+    for r in rows:
+        if r.get("mech") != "ldg" or r.get("status") or r.get("gbs_median") is None:
+            continue
+        g = (r["config"], r["gib"], r["cta"], r["grid"], r["order"])
+        groups.setdefault(g, {})[r["k"]] = r["gbs_median"]
+    for g, byk in sorted(groups.items()):
+        if 2 in byk and 8 in byk:
+            out.append({"config": g[0], "gib": g[1], "cta": g[2], "grid": g[3], "order": g[4],
+                        "k2": byk[2], "k8": byk[8], "change_pct": round(decline(byk[2], byk[8]), 2)})
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--config", required=True, choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu"])
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--repeats", type=int, default=10)
+    ap.add_argument("--orders", default="asc,desc")
+    a = ap.parse_args(argv)
+    t0 = time.time()
+    orders = ("asc",) if a.config == "ncu" else tuple(a.orders.split(","))
+    rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if a.config == "ncu" else 1)
+    for s in summarize(rows):
+        print(json.dumps({"summary": s}), flush=True)
+    print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,56 @@
+"""Host logic of the collection harness (no GPU): the endpoint-change formula
+against the paper's printed table, the cell grids of each configuration, and
+the resume keys."""
+import json
+import os
+
+import pytest
+
+from paper_2608_15764_gb300 import sweep
+
+
+def test_decline_matches_paper_table1(golden_dir):
+    """The printed bandwidths are rounded to 0.1 GB/s and the change to 0.1%,
+    so the formula must land inside the interval those roundings allow (the
+    first row, 3111.0 -> 1989.5 printed as -36.1%, is -36.05% from the rounded
+    inputs).  A wrong formula (another denominator, a sign flip) misses it by
+    whole percents."""
+    g = json.load(open(os.path.join(golden_dir, "paper_table1.json")))
+    for row in g["rows"]:
+        k2, k8 = row["k2_gbs"], row["k8_gbs"]
+        lo = sweep.decline(k2 + 0.05, k8 - 0.05)
+        hi = sweep.decline(k2 - 0.05, k8 + 0.05)
+        assert lo - 0.05 <= row["change_pct"] <= hi + 0.05, row["arm"]
+        assert abs(sweep.decline(k2, k8) - row["change_pct"]) < 0.06, row["arm"]
+    assert sweep.decline(100.0, 50.0) == -50.0 and sweep.decline(50.0, 100.0) == 100.0
+
+
+def test_cell_grids():
+    sms = 152
+    c1 = list(sweep._cells("c1", sms))
+    assert [c["k"] for c in c1] == [1, 2, 4, 8] and all(c["grid"] == 4 * sms and c["gib"] == 0.25 for c in c1)
+    c2 = list(sweep._cells("c2", sms))
+    assert len(c2) == 3 * 8 * 8
+    assert {c["grid"] for c in c2} == {r * sms for r in range(1, 9)}
+    assert {c["k"] for c in c2} == {1, 2, 3, 4, 6, 8, 12, 16}
+    c3 = list(sweep._cells("c3", sms))
+    assert sum(c["mech"] == "ldg" for c in c3) == 16 and sum(c["mech"] == "cpasync" for c in c3) == 8
+    assert sum(c["mech"] == "tma" for c in c3) == 21
+    c4 = list(sweep._cells("c4", sms))
+    assert sorted({c["gib"] for c in c4}) == [0.5, 1, 2, 4, 8, 16, 20]
+    prim = list(sweep._cells("primary", sms))
+    assert all(c["cta"] == 1024 and c["grid"] == sms for c in prim)  # 132 x 32 warps on H100 -> 152 x 32 here
+
+
+def test_resume_keys_distinguish_order():
+    c = next(sweep._cells("c1", 152))
+    assert sweep._key(c, "asc") != sweep._key(c, "desc")
+    assert json.loads(sweep._key(c, "asc"))["order"] == "asc"
+
+
+def test_summarize_endpoint_change():
+    rows = [{"config": "c1", "mech": "ldg", "status": 0, "gib": 1, "cta": 256, "grid": 608, "order": "asc",
+             "k": k, "gbs_median": v} for k, v in [(2, 3058.8), (8, 1988.7)]]
+    s = sweep.summarize(rows)
+    assert s == [{"config": "c1", "gib": 1, "cta": 256, "grid": 608, "order": "asc", "k2": 3058.8,
+                  "k8": 1988.7, "change_pct": -34.98}]
