@@ -6,7 +6,8 @@ the 129 MB L2, so no flush is needed between steps).  Before timing, the
 K-response curves of the three mechanisms (LDG K, cp.async D, TMA stage x
 stages) are measured on the same buffer and the fastest point is chosen
 (tune.choose).  One step = one checksum pass over the whole buffer with that
-point through ``sl_enqueue`` (load kernel + final combine kernel).
+point through ``sl_enqueue``: one load kernel, whose last CTA to finish
+combines the per-CTA partials into the result.
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
 
@@ -51,6 +52,9 @@ def _args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=1.5,
                     help="wall-clock seconds of the CPU-oracle sample (all cores)")
     ap.add_argument("--out", default=None, help="also append the JSON line (and curves) to this file")
+    ap.add_argument("--choice", default=None,
+                    help="skip the curves and time this point, e.g. 'ldg:6:256:0' (mech:K:cta:cop), "
+                         "'cpasync:5:256' or 'tma:16384:2:256' (tma:stage_bytes:stages:cta)")
     return ap.parse_args(argv)
 
 
@@ -122,6 +126,37 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    """Hash of the kernel sources: DRAM-traffic counters taken on another
+    version of the kernels are not reported."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2608_15764_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.startswith("k_") or name.endswith(".cuh") or name == "sl_internal.h":
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(label: str, nbytes: int):
+    """DRAM bytes per launch of the timed kernel from profiles/traffic.json
+    (captured on a smaller buffer; DRAM traffic of this streaming kernel grows
+    in proportion to the bytes read, so it is scaled to nbytes), or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(path))
+    except Exception:
+        return None, "no profiles/traffic.json"
+    if tj.get("kernel_source_hash") != kernel_source_hash():
+        return None, "kernels changed since the counters were taken"
+    e = tj.get("points", {}).get(label)
+    if not e:
+        return None, f"no capture for {label}"
+    return round(e["dram_bytes_per_launch"] * nbytes / e["bytes"]), \
+        f"scaled from a {e['bytes'] >> 20} MiB capture ({tj.get('command', '')})"
 
 
 def host_buffer(nbytes: int, pinned: bool):
@@ -218,7 +253,12 @@ def run_ours(a):
 
     # ---- K-response curves and the choice (rank 0 decides, all ranks follow)
     points = tune.default_points()
-    if rank == 0:
+    if a.choice:
+        points = [tune.parse_point(a.choice)]
+    if rank == 0 and a.choice:
+        tune.measure(buf, nbytes, points, repeats=1, warmup=1)
+        choice = [0]
+    elif rank == 0:
         tune.measure(buf, nbytes, points, repeats=a.curve_repeats, warmup=1)
         best = tune.choose(points)
         choice = [points.index(best)]
@@ -289,16 +329,7 @@ def run_ours(a):
     peak, peak_kind = _peaks()
     kern_ms = statistics.mean(step_ms)
     achieved = nbytes / (kern_ms * 1e6)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            key = best.label()
-            if key in tj and tj[key].get("bytes") == nbytes:
-                traffic = tj[key]["dram_bytes_per_launch"]
-        except Exception:
-            traffic = None
+    traffic, traffic_note = _traffic(best.label(), nbytes)
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 4), "higher_is_better": True,
@@ -311,13 +342,14 @@ def run_ours(a):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} copy (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback", "traffic": traffic,
-                     "note": "per-step CUDA-event time includes the 1-CTA combine kernel"},
+                     "traffic_note": traffic_note,
+                     "note": "per-step CUDA-event time of the load kernel, including its last-CTA combine"},
         "cpu_baseline": {"value": round(cpu_gbs, 2), "unit": "GB/s", "cores": threads, "kind": "oracle",
                          "sample": f"{passes} full passes over the {nbytes >> 20} MiB host buffer "
                                    f"({el:.1f} s wall, {threads} threads)"},
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": sl.RESULT_BYTES, "api": "sl_run_host (pinned host buffer, 256 MiB chunks)"},
-        "gpu_launches": 2 * a.steps,
+        "gpu_launches": a.steps,
         "clocks": clk,
         "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent)},
         "curves": [p.as_dict() for p in points],

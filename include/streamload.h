@@ -188,10 +188,10 @@ int sl_plan(uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out)
 int sl_run(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
            sl_result* out);
 
-/* As sl_run but asynchronous on cfg->stream: enqueues [L2 flush], the load
- * kernel and the combine kernel, which writes an sl_result (device_ns = 0,
- * launch-shape fields filled by the host) to the DEVICE pointer dev_out
- * (8-byte aligned).  Successive enqueues on one stream may share the
+/* As sl_run but asynchronous on cfg->stream: enqueues [L2 flush] and the
+ * load kernel, whose last CTA to finish combines all per-CTA partials (FP64
+ * for float sums) and writes an sl_result (device_ns and the launch-shape
+ * fields are 0) to the DEVICE pointer dev_out (8-byte aligned).  Successive enqueues on one stream may share the
  * library's scratch; enqueues on different streams at once race. */
 int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
                sl_result* dev_out);
@@ -231,9 +231,8 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
  * cudaMalloc, cudaFree or other allocating routine.  Its scratch (per-warp
  * partials, timestamps, the error word) is one fixed file-scope __device__
  * array of SL_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the
- * library until the process exits.  Limits: at most SL_NOALLOC_MAX_CTAS CTAs
- * and SL_NOALLOC_MAX_WARP_PARTIALS warps (CTAs x cta/32) per call; larger
- * launches are rejected with SL_ERR_ARG and a message.
+ * library until the process exits.  Limit: at most SL_NOALLOC_MAX_CTAS CTAs
+ * per call; larger launches are rejected with SL_ERR_ARG and a message.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
@@ -242,8 +241,7 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
  * call): calls whose work overlaps on the GPU (different streams, or other
  * threads) race and must be serialized by the caller. */
 #define SL_NOALLOC_MAX_CTAS 4096
-#define SL_NOALLOC_MAX_WARP_PARTIALS 32768
-#define SL_NOALLOC_SCRATCH_BYTES (SL_NOALLOC_MAX_WARP_PARTIALS * 32 + SL_NOALLOC_MAX_CTAS * 16 + 256)
+#define SL_NOALLOC_SCRATCH_BYTES (SL_NOALLOC_MAX_CTAS * 32 + 256)
 int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
                    sl_result* dev_out);
 

@@ -20,7 +20,7 @@ from ._abi import (  # noqa: F401  (re-exported constants)
     SL_ASC, SL_BF16, SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256, SL_CPASYNC,
     SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
     SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_MAX_D, SL_MAX_K,
-    SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_NOALLOC_MAX_WARP_PARTIALS, SL_OK, SL_TMA, SL_U32,
+    SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_TMA, SL_U32,
     STATUS_NAMES, RESULT_BYTES, load, sl_config, sl_devinfo, sl_result,
 )
 
@@ -170,8 +170,7 @@ def sl_run_noalloc(buf, dev_out, nbytes=None, dtype=SL_U32, cfg: sl_config | Non
     a no-allocation plugin contract).  Like sl_enqueue: asynchronous, result
     written to the device buffer dev_out (RESULT_BYTES).  Scratch is a fixed
     device array shared by every call on the device: calls that overlap on
-    the GPU race.  Launches above SL_NOALLOC_MAX_CTAS CTAs or
-    SL_NOALLOC_MAX_WARP_PARTIALS warps are rejected."""
+    the GPU race.  Launches above SL_NOALLOC_MAX_CTAS CTAs are rejected."""
     cfg = cfg or config()
     _check(load().sl_run_noalloc(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg),
                                  _addr(dev_out)))

@@ -120,7 +120,6 @@ PROTOTYPES = {
     "sl_run_noalloc": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), _P]),
 }
 SL_NOALLOC_MAX_CTAS = 4096
-SL_NOALLOC_MAX_WARP_PARTIALS = 32768
 
 _lock = threading.Lock()
 _lib = None

@@ -72,9 +72,7 @@ struct DevCtx {
     sl_devinfo info{};
     WarpPartial* parts = nullptr;
     uint64_t parts_cap = 0;
-    uint64_t* tstamp = nullptr;
-    uint64_t ts_cap = 0;
-    uint32_t* err = nullptr;
+    uint32_t* err = nullptr;    // control block (sl::CTRL_BYTES): error word, CTA counter, window
     sl_result* dres = nullptr;  // device result of sl_run / sl_run_host
     sl_result* hres = nullptr;  // pinned host copy
     void* flush = nullptr;
@@ -133,8 +131,9 @@ int get_ctx(DevCtx** out) {
         c->dev = dev;
         int rc = query_info(dev, &c->info);
         if (rc) return rc;
-        CUDA_TRY(cudaMalloc(&c->err, sizeof(uint32_t)));
-        CUDA_TRY(cudaMemset(c->err, 0, sizeof(uint32_t)));
+        CUDA_TRY(cudaMalloc(&c->err, sl::CTRL_BYTES));
+        CUDA_TRY(cudaMemset(c->err, 0, sl::CTRL_BYTES));
+        CUDA_TRY(cudaMemset(sl::ctrl_window(c->err), 0xFF, sizeof(uint64_t)));  // earliest start = ~0
         CUDA_TRY(cudaMalloc(&c->dres, sizeof(sl_result)));
         CUDA_TRY(cudaMallocHost(&c->hres, sizeof(sl_result)));
         CUDA_TRY(cudaEventCreate(&c->ev0));
@@ -149,9 +148,9 @@ int get_ctx(DevCtx** out) {
     return SL_OK;
 }
 
-// Grow the partial / timestamp scratch.  Growing waits for the device to go
-// idle first, since enqueued work may still use the old buffers.
-int ensure_scratch(DevCtx* c, uint64_t nparts, uint64_t nctas) {
+// Grow the per-CTA partial scratch.  Growing waits for the device to go idle
+// first, since enqueued work may still use the old buffer.
+int ensure_scratch(DevCtx* c, uint64_t nparts) {
     if (nparts > c->parts_cap) {
         uint64_t cap = std::max<uint64_t>(nparts, 1 << 16);
         CUDA_TRY(cudaDeviceSynchronize());
@@ -160,15 +159,6 @@ int ensure_scratch(DevCtx* c, uint64_t nparts, uint64_t nctas) {
         c->parts_cap = 0;
         CUDA_TRY(cudaMalloc(&c->parts, cap * sizeof(WarpPartial)));
         c->parts_cap = cap;
-    }
-    if (nctas > c->ts_cap) {
-        uint64_t cap = std::max<uint64_t>(nctas, 1 << 14);
-        CUDA_TRY(cudaDeviceSynchronize());
-        if (c->tstamp) CUDA_TRY(cudaFree(c->tstamp));
-        c->tstamp = nullptr;
-        c->ts_cap = 0;
-        CUDA_TRY(cudaMalloc(&c->tstamp, 2 * cap * sizeof(uint64_t)));
-        c->ts_cap = cap;
     }
     return SL_OK;
 }
@@ -192,7 +182,7 @@ int func_info(DevCtx* c, const void* fn, size_t smem, FuncInfo** out) {
         fi.local_bytes = fa.localSizeBytes;
         fi.regs = fa.numRegs;
     }
-    if (smem > 48 * 1024 && fi.smem_attr < smem) {
+    if (smem > 0 && fi.smem_attr < smem) {  // static smem counts too: opt in for any dynamic size
         CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
         fi.smem_attr = smem;
     }
@@ -334,18 +324,20 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
     int rc = make_plan(c, buf, bytes, dtype, cfg, &p);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
-    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid), static_cast<uint64_t>(p.grid));
+    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid));
     if (rc) return rc;
     p.args.parts = c->parts;
-    p.args.tstamp = c->tstamp;
-    p.args.err = c->err;
+    p.args.window = sl::ctrl_window(c->err);
+    p.args.err = sl::ctrl_err(c->err);
+    p.args.done = sl::ctrl_done(c->err);
+    p.args.result = dev_out;  // the kernel's last CTA writes the result
     if (cfg->flush_l2) CUDA_TRY(sl::launch_flush(c->flush, c->flush_bytes / 16, c->info.sm_count, s));
     if (events) CUDA_TRY(cudaEventRecord(c->ev0, s));
     rc = launch(p, s);
     if (rc) return rc;
     if (events) CUDA_TRY(cudaEventRecord(c->ev1, s));
-    CUDA_TRY(sl::launch_combine(c->parts, static_cast<uint64_t>(p.grid), c->tstamp,
-                                static_cast<uint64_t>(p.grid), c->err, dev_out, s));
+    if (p.grid == 0)  // empty buffer: no load kernel, the combine writes the zero result
+        CUDA_TRY(sl::launch_combine(c->parts, 0, sl::ctrl_window(c->err), c->err, dev_out, s));
     if (plan_out) *plan_out = p;
     return SL_OK;
 }
@@ -498,7 +490,7 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
     rc = make_plan(c, c->stage[0], chunk, dtype, cfg, &p);
     if (rc) return rc;
     const uint64_t per_parts = static_cast<uint64_t>(p.grid);  // one partial per CTA
-    rc = ensure_scratch(c, per_parts * nchunks, static_cast<uint64_t>(p.grid) * nchunks);
+    rc = ensure_scratch(c, per_parts * nchunks);
     if (rc) return rc;
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
 
@@ -520,14 +512,15 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
         a.ntiles = (nvec + a.tile_vec - 1) / a.tile_vec;
         a.total = a.ntiles * passes;
         a.parts = c->parts + i * per_parts;
-        a.tstamp = c->tstamp + 2 * i * static_cast<uint64_t>(p.grid);
+        a.window = sl::ctrl_window(c->err);
         a.err = c->err;
+        a.result = nullptr;  // combined over all chunks below
+        a.done = nullptr;
         void* args[] = {&a};
         CUDA_TRY(cudaLaunchKernel(p.fn, dim3(static_cast<unsigned>(p.grid)), dim3(p.block), args, p.smem, s));
         CUDA_TRY(cudaEventRecord(c->consumed[b], s));
     }
-    CUDA_TRY(sl::launch_combine(c->parts, per_parts * nchunks, c->tstamp, static_cast<uint64_t>(p.grid) * nchunks,
-                                c->err, c->dres, s));
+    CUDA_TRY(sl::launch_combine(c->parts, per_parts * nchunks, sl::ctrl_window(c->err), c->err, c->dres, s));
     CUDA_TRY(cudaMemcpyAsync(c->hres, c->dres, sizeof(sl_result), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaEventRecord(c->ev1, s));
     CUDA_TRY(cudaStreamSynchronize(s));

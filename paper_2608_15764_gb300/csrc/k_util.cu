@@ -38,25 +38,24 @@ __global__ void __launch_bounds__(256) k_flush(uint4* __restrict__ buf, uint64_t
         buf[j] = make_uint4(tag, static_cast<uint32_t>(j), 0u, 0u);
 }
 
-// Final combine of per-CTA partials into one sl_result.  One CTA of
+// Final combine of per-CTA partials into one sl_result, as a separate
+// launch (used when the load kernels do not combine in their last CTA: the
+// multi-chunk host-buffer path, and empty buffers).  One CTA of
 // COMBINE_THREADS threads; thread i folds partials i, i+T, ... in index order,
 // then a fixed shared-memory tree merges the threads, so the FP64 float sum
-// has a fixed order (deterministic for a given launch shape).  Integer parts
-// combine exactly.  The device error word is reported in status and cleared.
+// has a fixed order.  Integer parts combine exactly.  The device error word is
+// reported in status and cleared; the timing window is read and reset.
 constexpr int COMBINE_THREADS = 512;
 
 __global__ void __launch_bounds__(COMBINE_THREADS) k_combine(const WarpPartial* __restrict__ parts,
-                                                            uint64_t nparts,
-                                                            const uint64_t* __restrict__ tstamp,
-                                                            uint64_t nctas, uint32_t* err,
-                                                            sl_result* out) {
+                                                            uint64_t nparts, uint64_t* window,
+                                                            uint32_t* err, sl_result* out) {
     __shared__ uint32_t s_sum[COMBINE_THREADS];
     __shared__ uint64_t s_xor[COMBINE_THREADS], s_n[COMBINE_THREADS];
-    __shared__ uint64_t s_t0[COMBINE_THREADS], s_t1[COMBINE_THREADS];
     __shared__ double s_f[COMBINE_THREADS];
     const int t = threadIdx.x;
     uint32_t sum = 0;
-    uint64_t xr = 0, n = 0, t0 = ~0ull, t1 = 0;
+    uint64_t xr = 0, n = 0;
     double f = 0.0;
     for (uint64_t i = t; i < nparts; i += COMBINE_THREADS) {
         const WarpPartial p = parts[i];
@@ -65,16 +64,10 @@ __global__ void __launch_bounds__(COMBINE_THREADS) k_combine(const WarpPartial* 
         n += p.issued;
         f += static_cast<double>(p.hi) + static_cast<double>(p.lo);
     }
-    for (uint64_t i = t; i < nctas; i += COMBINE_THREADS) {
-        t0 = min(t0, tstamp[2 * i]);
-        t1 = max(t1, tstamp[2 * i + 1]);
-    }
     s_sum[t] = sum;
     s_xor[t] = xr;
     s_n[t] = n;
     s_f[t] = f;
-    s_t0[t] = t0;
-    s_t1[t] = t1;
     __syncthreads();
     for (int w = COMBINE_THREADS / 2; w > 0; w >>= 1) {
         if (t < w) {
@@ -82,17 +75,16 @@ __global__ void __launch_bounds__(COMBINE_THREADS) k_combine(const WarpPartial* 
             s_xor[t] ^= s_xor[t + w];
             s_n[t] += s_n[t + w];
             s_f[t] += s_f[t + w];
-            s_t0[t] = min(s_t0[t], s_t0[t + w]);
-            s_t1[t] = max(s_t1[t], s_t1[t + w]);
         }
         __syncthreads();
     }
     if (t == 0) {
+        const uint64_t t0 = window[0], t1 = window[1];
         sl_result r;
         r.xor_u64 = s_xor[0];
         r.issued_loads = s_n[0];
         r.device_ns = 0;
-        r.window_ns = (nctas > 0 && s_t1[0] > s_t0[0]) ? s_t1[0] - s_t0[0] : 0;
+        r.window_ns = (nparts > 0 && t1 > t0) ? t1 - t0 : 0;
         r.fsum = s_f[0];
         r.fsum_hi = static_cast<float>(s_f[0]);
         r.fsum_lo = static_cast<float>(s_f[0] - static_cast<double>(r.fsum_hi));
@@ -105,6 +97,8 @@ __global__ void __launch_bounds__(COMBINE_THREADS) k_combine(const WarpPartial* 
         r.smem_bytes = 0;
         *out = r;
         *err = 0;
+        window[0] = ~0ull;
+        window[1] = 0;
     }
 }
 
@@ -126,9 +120,9 @@ cudaError_t launch_flush(void* buf, uint64_t nvec, int sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine(const WarpPartial* parts, uint64_t nparts, const uint64_t* tstamp,
-                           uint64_t nctas, uint32_t* err, sl_result* out, cudaStream_t s) {
-    k_combine<<<1, COMBINE_THREADS, 0, s>>>(parts, nparts, tstamp, nctas, err, out);
+cudaError_t launch_combine(const WarpPartial* parts, uint64_t nparts, uint64_t* window, uint32_t* err,
+                           sl_result* out, cudaStream_t s) {
+    k_combine<<<1, COMBINE_THREADS, 0, s>>>(parts, nparts, window, err, out);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@
 // The regular entry points allocate their scratch lazily (and may grow it,
 // which synchronizes the device), so such callers cannot use them.
 //
-// Here the scratch -- per-warp partials, per-CTA timestamps and the device
-// error word -- lives in one file-scope __device__ array of fixed size
+// Here the scratch -- per-CTA partials and a 256-byte control block (device
+// error word, finished-CTA counter, timing window) -- lives in one file-scope
+// __device__ array of fixed size
 // (SL_NOALLOC_SCRATCH_BYTES).  Every GPU that loads this library holds that
 // array until the process exits.  Host code never uses the array's name as an
 // address (on the host it is only a stand-in); it asks the runtime for the
@@ -23,17 +24,15 @@
 
 namespace {
 
-constexpr uint64_t NA_MAX_PARTS = SL_NOALLOC_MAX_WARP_PARTIALS;
 constexpr uint64_t NA_MAX_CTAS = SL_NOALLOC_MAX_CTAS;
 constexpr uint64_t NA_PARTS_OFF = 0;
-constexpr uint64_t NA_TS_OFF = NA_PARTS_OFF + NA_MAX_PARTS * sizeof(sl::WarpPartial);
-constexpr uint64_t NA_ERR_OFF = NA_TS_OFF + 2 * NA_MAX_CTAS * sizeof(uint64_t);
-constexpr uint64_t NA_BYTES = NA_ERR_OFF + 256;
+constexpr uint64_t NA_CTRL_OFF = NA_PARTS_OFF + NA_MAX_CTAS * sizeof(sl::WarpPartial);
+constexpr uint64_t NA_BYTES = NA_CTRL_OFF + sl::CTRL_BYTES;
 static_assert(NA_BYTES == SL_NOALLOC_SCRATCH_BYTES, "scratch layout");
 
 // The fixed scratch.  Shared by every sl_run_noalloc call on a device; it
-// keeps the previous call's contents, so the error word is cleared before
-// each launch (partials and timestamps are fully rewritten by the kernel).
+// keeps the previous call's contents, so the control block is cleared before
+// each launch (the partials are fully rewritten by the kernel).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SL_NOALLOC_SCRATCH_BYTES];
 
 constexpr int NA_MAX_DEVICES = 64;
@@ -100,10 +99,8 @@ extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype
     if (resident < 1) return na_fail(SL_ERR_INFEASIBLE, "zero occupancy");
     const uint64_t grid = cfg->grid > 0 ? static_cast<uint64_t>(cfg->grid)
                                         : static_cast<uint64_t>(resident < 4 ? resident : 4) * sms;
-    const uint64_t nparts = grid * static_cast<uint64_t>(cta / 32);
-    if (grid > NA_MAX_CTAS || nparts > NA_MAX_PARTS)
-        return na_fail(SL_ERR_ARG, "launch exceeds the fixed scratch: at most SL_NOALLOC_MAX_CTAS CTAs and "
-                                   "SL_NOALLOC_MAX_WARP_PARTIALS warps (CTAs x cta/32)");
+    if (grid > NA_MAX_CTAS)
+        return na_fail(SL_ERR_ARG, "launch exceeds the fixed scratch: at most SL_NOALLOC_MAX_CTAS (4096) CTAs");
 
     {
         const uint64_t tv = static_cast<uint64_t>(cta) * cfg->k;
@@ -115,13 +112,14 @@ extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype
     int rc = scratch_for(dev, &base);
     if (rc) return rc;
     sl::WarpPartial* parts = reinterpret_cast<sl::WarpPartial*>(base + NA_PARTS_OFF);
-    uint64_t* tstamp = reinterpret_cast<uint64_t*>(base + NA_TS_OFF);
-    uint32_t* err = reinterpret_cast<uint32_t*>(base + NA_ERR_OFF);
+    void* ctrl = base + NA_CTRL_OFF;
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
 
-    if (cudaMemsetAsync(err, 0, sizeof(uint32_t), s) != cudaSuccess) {
+    // error word and CTA counter start at zero, the window at (~0, 0)
+    if (cudaMemsetAsync(ctrl, 0, sl::CTRL_BYTES, s) != cudaSuccess ||
+        cudaMemsetAsync(sl::ctrl_window(ctrl), 0xFF, sizeof(uint64_t), s) != cudaSuccess) {
         (void)cudaGetLastError();
-        return na_fail(SL_ERR_CUDA, "clearing the error word failed");
+        return na_fail(SL_ERR_CUDA, "clearing the control block failed");
     }
     const uint64_t nvec = bytes / 16;
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
@@ -136,16 +134,19 @@ extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype
         a.tile_vec = static_cast<uint32_t>(tile_vec);
         a.desc = cfg->order == SL_DESC ? 1 : 0;
         a.parts = parts;
-        a.tstamp = tstamp;
-        a.err = err;
+        a.window = sl::ctrl_window(ctrl);
+        a.err = sl::ctrl_err(ctrl);
         a.timeout_ns = 2000000000ull;
+        a.result = dev_out;  // the last CTA writes the result
+        a.done = sl::ctrl_done(ctrl);
         void* args[] = {&a};
         if (cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(cta), args, 0, s) != cudaSuccess) {
             (void)cudaGetLastError();
             return na_fail(SL_ERR_CUDA, "kernel launch failed");
         }
     }
-    if (sl::launch_combine(parts, launched, tstamp, launched, err, dev_out, s) != cudaSuccess) {
+    if (!launched &&
+        sl::launch_combine(parts, 0, sl::ctrl_window(ctrl), sl::ctrl_err(ctrl), dev_out, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return na_fail(SL_ERR_CUDA, "combine launch failed");
     }

@@ -169,12 +169,90 @@ __device__ __forceinline__ void warp_merge(uint32_t& s, uint64_t& x, uint64_t& n
     }
 }
 
+// Final combine of all CTAs' partials into one sl_result, run by the whole
+// CTA that finished last: thread t folds partials t, t+blockDim, ... in index
+// order (FP64 for the float part: (double)hi + (double)lo), then the warps
+// and the per-warp results are merged by fixed shuffle butterflies, so the
+// float sum has a fixed order for a given launch shape.  Integer parts are
+// exact.  The device error word becomes the status and is cleared; the CTA
+// counter and the timing window are reset for the next launch.
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_all(T v, Op op) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(FULL_MASK, v, o));
+    return v;
+}
+
+// Loops are not unrolled and each field is reduced on its own, so that this
+// code needs fewer registers than the streaming loop it follows.
+__device__ __forceinline__ void final_combine(const KArgs& a) {
+    struct Fin {
+        uint32_t sum;
+        uint64_t x, n;
+        double f;
+    };
+    __shared__ Fin fw[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const uint32_t n = gridDim.x;
+    Fin v{0u, 0ull, 0ull, 0.0};
+#pragma unroll 1
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint4 lo4 = __ldcg(reinterpret_cast<const uint4*>(a.parts + i));
+        const uint4 hi4 = __ldcg(reinterpret_cast<const uint4*>(a.parts + i) + 1);
+        v.sum += lo4.x;
+        v.x ^= (static_cast<uint64_t>(lo4.w) << 32) | lo4.z;
+        v.n += (static_cast<uint64_t>(hi4.y) << 32) | hi4.x;
+        v.f += static_cast<double>(__uint_as_float(hi4.z)) + static_cast<double>(__uint_as_float(hi4.w));
+    }
+    const auto add32 = [](uint32_t p, uint32_t q) { return p + q; };
+    const auto add64 = [](uint64_t p, uint64_t q) { return p + q; };
+    const auto xor64 = [](uint64_t p, uint64_t q) { return p ^ q; };
+    const auto addf = [](double p, double q) { return p + q; };
+    for (int pass = 0; pass < 2; ++pass) {  // pass 0: within warps; pass 1: across warps (warp 0)
+        v.sum = warp_all(v.sum, add32);
+        v.x = warp_all(v.x, xor64);
+        v.n = warp_all(v.n, add64);
+        v.f = warp_all(v.f, addf);
+        if (pass == 1) break;
+        if (lane == 0) fw[warp] = v;
+        __syncthreads();
+        if (warp != 0) return;
+        v = lane < nw ? fw[lane] : Fin{0u, 0ull, 0ull, 0.0};
+    }
+    if (lane == 0) {
+        // field by field: a whole sl_result in registers would raise the
+        // kernel's register count
+        sl_result* r = a.result;
+        r->xor_u64 = v.x;
+        r->issued_loads = v.n;
+        r->device_ns = 0;
+        volatile uint64_t* w = a.window;
+        const uint64_t t0 = w[0], t1 = w[1];
+        r->window_ns = t1 > t0 ? t1 - t0 : 0;
+        r->fsum = v.f;
+        const float hi = static_cast<float>(v.f);
+        r->fsum_hi = hi;
+        r->fsum_lo = static_cast<float>(v.f - static_cast<double>(hi));
+        r->sum_u32 = v.sum;
+        r->status = *reinterpret_cast<volatile uint32_t*>(a.err) ? SL_ERR_TIMEOUT : SL_OK;
+        r->grid = 0;
+        r->cta = 0;
+        r->resident_per_sm = 0;
+        r->smem_bytes = 0;
+        *a.err = 0;
+        *a.done = 0;
+        w[0] = ~0ull;
+        w[1] = 0;
+    }
+}
+
 // End of a streaming kernel: every folding warp (all 32 lanes present)
 // reduces its accumulators and lane 0 puts the warp partial in shared memory;
 // after a CTA barrier warp 0 merges the warp partials (butterfly, fixed
-// order) into the CTA's partial a.parts[blockIdx.x], and thread 0 stores the
-// CTA's start/end %globaltimer stamps.  `fw` is this warp's index among the
-// nfw (<= 32) folding warps.
+// order) into the CTA's partial a.parts[blockIdx.x], and thread 0 raises the
+// launch's end stamp to this CTA's %globaltimer.  With
+// a.result set, the last CTA to get here then runs final_combine.  `fw` is
+// this warp's index among the nfw (<= 32) folding warps.
 template <int DT>
 __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint32_t fw, uint32_t nfw,
                                            const KArgs& a) {
@@ -219,8 +297,21 @@ __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint3
             p.hi = hi;
             p.lo = lo;
             a.parts[blockIdx.x] = p;
-            a.tstamp[2 * blockIdx.x + 1] = gtimer();
+            atomicMax(reinterpret_cast<unsigned long long*>(a.window + 1), gtimer());
         }
+    }
+    if (a.result == nullptr) return;
+    // Last-CTA-done: publish this CTA's partial, count it, and let the CTA
+    // that completes the count combine everything.
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        final_combine(a);
     }
 }
 
@@ -243,10 +334,10 @@ struct TileCursor {
     }
 };
 
-// Start of a streaming kernel: thread 0 stores the CTA's start %globaltimer
-// stamp (no register holds it through the kernel).
+// Start of a streaming kernel: thread 0 lowers the launch's start stamp to
+// this CTA's %globaltimer (no register holds it through the kernel).
 __device__ __forceinline__ void cta_start(const KArgs& a) {
-    if (threadIdx.x == 0) a.tstamp[2 * blockIdx.x] = gtimer();
+    if (threadIdx.x == 0) atomicMin(reinterpret_cast<unsigned long long*>(a.window), gtimer());
 }
 
 }  // namespace sl

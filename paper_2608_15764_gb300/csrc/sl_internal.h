@@ -33,9 +33,14 @@ struct KArgs {
     int32_t nst;            // TMA: ring stages
     int32_t debug;          // SL_DEBUG_* flags
     WarpPartial* parts;     // [grid]: one partial per CTA
-    uint64_t* tstamp;       // [2 * grid]: %globaltimer at CTA start / end
+    uint64_t* window;       // [2]: earliest CTA start, latest CTA end
+                            // (%globaltimer; ~0 and 0 before the launch)
     uint32_t* err;          // device error word (0 = fine)
     uint64_t timeout_ns;    // bound of any single device wait
+    sl_result* result;      // if set: the last CTA to finish combines all
+                            // partials into *result (else a separate combine)
+    uint32_t* done;         // CTAs finished (zero before the launch; the last
+                            // CTA resets it)
 };
 
 // Device error codes written to *err (first writer wins).
@@ -54,7 +59,14 @@ int set_error(int code, const char* msg);
 // Utility launches (k_util.cu); asynchronous on `s`.
 cudaError_t launch_fill_splitmix64(void* buf, uint64_t nvec, uint64_t seed, int sms, cudaStream_t s);
 cudaError_t launch_flush(void* buf, uint64_t nvec, int sms, cudaStream_t s);
-cudaError_t launch_combine(const WarpPartial* parts, uint64_t nparts, const uint64_t* tstamp,
-                           uint64_t nctas, uint32_t* err, sl_result* out, cudaStream_t s);
+cudaError_t launch_combine(const WarpPartial* parts, uint64_t nparts, uint64_t* window, uint32_t* err,
+                           sl_result* out, cudaStream_t s);
+
+// Layout of the 256-byte control block shared by a launch and its combine:
+// error word at byte 0, finished-CTA counter at byte 64, window at byte 128.
+constexpr int CTRL_BYTES = 256;
+inline uint32_t* ctrl_err(void* c) { return static_cast<uint32_t*>(c); }
+inline uint32_t* ctrl_done(void* c) { return static_cast<uint32_t*>(c) + 16; }
+inline uint64_t* ctrl_window(void* c) { return static_cast<uint64_t*>(c) + 16; }
 
 }  // namespace sl

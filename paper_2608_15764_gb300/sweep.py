@@ -25,6 +25,10 @@ GPU and checked against the first cell's checksum):
   ncu  a small case for counter captures (1 GiB, one launch per cell, no
        warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), cp.async D=8, TMA
        16 KiB x 2 stages.
+  ncu-points  every candidate point of the benchmark (tune.default_points)
+       on 1 GiB, then LDG K=2 and K=8 on 512 MiB and 2 GiB (one launch each,
+       no warm-up): DRAM bytes per launch for the roofline, and the paper's
+       counter audit (§4.2) across allocation sizes.
 
     python -m paper_2608_15764_gb300.sweep --config c2 --out runs.jsonl [--repeats 10]
 
@@ -79,6 +83,16 @@ def _cells(config: str, sms: int):
     elif config == "primary":
         for k in (1, 2, 4, 8):
             yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=4)
+    elif config == "ncu-points":
+        from .tune import default_points
+        for p in default_points():
+            if p.mech == 2:
+                yield dict(mech="tma", stage_bytes=p.stage_bytes, stages=p.stages, cta=p.cta, grid=0, gib=1)
+            else:
+                yield dict(mech="ldg" if p.mech == 0 else "cpasync", k=p.k, cta=p.cta, grid=0, cop=p.cop, gib=1)
+        for gib in (0.5, 2):
+            for k in (2, 8):
+                yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
     elif config == "ncu":
         yield dict(mech="ldg", k=2, cta=256, grid=4 * sms, gib=1)
         yield dict(mech="ldg", k=8, cta=256, grid=4 * sms, gib=1)
@@ -132,7 +146,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                 if c["mech"] == "tma":
                     cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
                 else:
-                    cfg = sl.config(c["mech"], k=c["k"], **kw)
+                    cfg = sl.config(c["mech"], k=c["k"], cop=c.get("cop", 0), **kw)
                 status, resident = 0, 0
                 try:
                     plan = sl.sl_plan(nbytes, sl.SL_U32, cfg)
@@ -208,14 +222,16 @@ def summarize(rows):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--config", required=True, choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu"])
+    ap.add_argument("--config", required=True,
+                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
     a = ap.parse_args(argv)
     t0 = time.time()
-    orders = ("asc",) if a.config == "ncu" else tuple(a.orders.split(","))
-    rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if a.config == "ncu" else 1)
+    ncu = a.config.startswith("ncu")
+    orders = ("asc",) if ncu else tuple(a.orders.split(","))
+    rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if ncu else 1)
     for s in summarize(rows):
         print(json.dumps({"summary": s}), flush=True)
     print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)

@@ -67,6 +67,18 @@ class Point:
         return d
 
 
+def parse_point(text: str) -> Point:
+    """'ldg:K:cta[:cop]', 'cpasync:D:cta' or 'tma:stage_bytes:stages:cta'."""
+    f = text.split(":")
+    mech = f[0]
+    if mech == "tma":
+        return Point(SL_TMA, stage_bytes=int(f[1]), stages=int(f[2]), cta=int(f[3]) if len(f) > 3 else 256)
+    if mech in ("ldg", "cpasync"):
+        return Point(SL_LDG if mech == "ldg" else SL_CPASYNC, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256,
+                     cop=int(f[3]) if len(f) > 3 else 0)
+    raise ValueError(f"bad point {text!r}")
+
+
 def default_points(cta: int = 256) -> list[Point]:
     pts = [Point(SL_LDG, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8, 12, 16)]
     pts += [Point(SL_LDG, k=k, cta=cta, cop=1) for k in (1, 2, 4, 8)]

@@ -64,7 +64,7 @@ def test_noalloc_limits_and_empty(sl):
     dev = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
     out = torch.zeros(sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     for cfg in [sl.config("ldg", k=1, cta=256, grid=sl.SL_NOALLOC_MAX_CTAS + 1),
-                sl.config("ldg", k=1, cta=1024, grid=2048),   # 65,536 warps > the fixed scratch
+                sl.config("ldg", k=1, cta=1024, grid=10000),  # more CTAs than the fixed scratch holds
                 sl.config("tma"), sl.config("ldg", flush_l2=True)]:
         with pytest.raises(sl.SLError) as e:
             sl.sl_run_noalloc(dev, out, dtype=sl.SL_U32, cfg=cfg)
