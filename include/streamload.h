@@ -215,6 +215,62 @@ int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
                 sl_result* out);
 
+/* ---- batched form -------------------------------------------------------- */
+
+/* One device buffer of a batch (24 bytes). */
+typedef struct sl_batch_desc {
+    const void* ptr;    /* device address, 16-byte aligned (caller-owned) */
+    uint64_t    bytes;  /* a multiple of 16; 0 gives an all-zero result */
+    int32_t     dtype;  /* sl_dtype */
+    int32_t     reserved;
+} sl_batch_desc;
+
+/* One size class of the tuning table: buffers with min_bytes <= bytes <=
+ * max_bytes (and dtype == dtype, or dtype == -1 for any) run with cfg.  In
+ * cfg: mech, k (LDG K in {1,2,3,4,6,8,12,16}, cp.async D 1..8), stage_bytes,
+ * stages, cta (LDG: 128/256/512) and grid (<= 0: resident CTAs per SM x
+ * SMs, a persistent grid) are used; order, passes, flush_l2, cop,
+ * debug_flags and stream are ignored. */
+typedef struct sl_tune_entry {
+    uint64_t  min_bytes;
+    uint64_t  max_bytes;
+    int32_t   dtype;
+    int32_t   reserved;
+    sl_config cfg;
+} sl_tune_entry;
+
+typedef struct sl_batch sl_batch;  /* opaque */
+
+/* Build a batched streaming checksum over n buffers (spec form 2: a
+ * persistent kernel per size class streaming many uneven buffers, in one
+ * CUDA-graph launch; no paper counterpart).  Each buffer goes to the first
+ * table entry that matches it (SL_ERR_ARG if none).  Buffers are cut into
+ * work items of at most 1 MiB; each class kernel runs a persistent grid whose
+ * CTAs claim items from an atomic counter, fold them with the class's
+ * mechanism and write one partial per warp per item; a combine kernel with
+ * one warp per buffer adds each buffer's partials (integer parts exactly,
+ * float parts in FP64, in a fixed order) into its sl_result.  The graph --
+ * a memset of the counters, the class kernels as parallel branches, then the
+ * combine -- is captured once here and replayed by sl_batch_run.  The batch
+ * owns its device tables, results, streams and graph until sl_batch_destroy;
+ * the caller keeps the buffers alive and unchanged in size.  Asynchronous
+ * work of other calls must not overlap a batch run on the same buffers'
+ * device (the class kernels may fill the whole GPU). */
+int sl_batch_create(const sl_batch_desc* descs, int32_t n, const sl_tune_entry* table, int32_t ntable,
+                    sl_batch** out);
+
+/* Launch the batch's graph once and wait.  per_buffer (host, n entries, may
+ * be NULL to skip the copy-back) receives each buffer's result in descriptor
+ * order (device_ns = 0 in each); *total_ns (may be NULL) receives the
+ * CUDA-event time of the whole graph launch. */
+int sl_batch_run(sl_batch* b, sl_result* per_buffer, uint64_t* total_ns);
+
+/* Number of class kernels (graph kernel nodes besides the combine) and the
+ * class each buffer went to (host array of n, may be NULL). */
+int sl_batch_info(const sl_batch* b, int32_t* nclasses, int32_t* class_of_buffer);
+
+void sl_batch_destroy(sl_batch* b);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* The paper has no counterpart to this entry point; it exists for callers of

@@ -21,7 +21,7 @@ from ._abi import (  # noqa: F401  (re-exported constants)
     SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
     SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_MAX_D, SL_MAX_K,
     SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_TMA, SL_U32,
-    STATUS_NAMES, RESULT_BYTES, load, sl_config, sl_devinfo, sl_result,
+    STATUS_NAMES, RESULT_BYTES, load, sl_batch_desc, sl_config, sl_devinfo, sl_result, sl_tune_entry,
 )
 
 MECHS = {"ldg": SL_LDG, "cpasync": SL_CPASYNC, "tma": SL_TMA}
@@ -174,3 +174,70 @@ def sl_run_noalloc(buf, dev_out, nbytes=None, dtype=SL_U32, cfg: sl_config | Non
     cfg = cfg or config()
     _check(load().sl_run_noalloc(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg),
                                  _addr(dev_out)))
+
+
+def tune_entry(min_bytes: int, max_bytes: int, cfg: sl_config, dtype: int = -1) -> sl_tune_entry:
+    """One size class of a batch's tuning table (dtype -1 matches any)."""
+    e = sl_tune_entry()
+    e.min_bytes = int(min_bytes)
+    e.max_bytes = int(max_bytes)
+    e.dtype = int(dtype)
+    e.cfg = cfg
+    return e
+
+
+class sl_batch:
+    """Handle of a batch built by sl_batch_create (sl_batch_destroy frees it;
+    so does garbage collection)."""
+
+    def __init__(self, handle: int, n: int, nbytes: int, keepalive):
+        self.handle = handle
+        self.n = n
+        self.nbytes = nbytes
+        self._keep = keepalive
+
+    def __del__(self):
+        try:
+            sl_batch_destroy(self)
+        except Exception:  # pragma: no cover
+            pass
+
+
+def sl_batch_create(buffers, table) -> sl_batch:
+    """buffers: sequence of (device buffer or address, nbytes, dtype);
+    table: sequence of sl_tune_entry (see tune_entry)."""
+    n = len(buffers)
+    descs = (sl_batch_desc * max(n, 1))()
+    total = 0
+    for i, (buf, nb, dt) in enumerate(buffers):
+        descs[i].ptr = _addr(buf)
+        descs[i].bytes = int(nb)
+        descs[i].dtype = _dtype(dt)
+        total += int(nb)
+    tab = (sl_tune_entry * len(table))(*table)
+    h = ctypes.c_void_p()
+    _check(load().sl_batch_create(descs, n, tab, len(table), ctypes.byref(h)))
+    return sl_batch(h.value, n, total, [b for b, _, _ in buffers])
+
+
+def sl_batch_run(b: sl_batch, results: bool = True):
+    """Launch the batch's graph once; returns (list of per-buffer sl_result or
+    None, device ns of the graph launch)."""
+    out = (sl_result * max(b.n, 1))() if results else None
+    ns = ctypes.c_uint64()
+    _check(load().sl_batch_run(b.handle, out, ctypes.byref(ns)))
+    return ([out[i] for i in range(b.n)] if results else None), int(ns.value)
+
+
+def sl_batch_info(b: sl_batch):
+    """(number of class kernels, class index of every buffer)."""
+    nc = ctypes.c_int32()
+    cls = (ctypes.c_int32 * max(b.n, 1))()
+    _check(load().sl_batch_info(b.handle, ctypes.byref(nc), cls))
+    return int(nc.value), [cls[i] for i in range(b.n)]
+
+
+def sl_batch_destroy(b: sl_batch) -> None:
+    if b.handle:
+        load().sl_batch_destroy(b.handle)
+        b.handle = None

@@ -99,6 +99,18 @@ class sl_devinfo(ctypes.Structure):
         return d
 
 
+class sl_batch_desc(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("bytes", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class sl_tune_entry(ctypes.Structure):
+    _fields_ = [("min_bytes", ctypes.c_uint64), ("max_bytes", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("cfg", sl_config)]
+
+
+assert ctypes.sizeof(sl_batch_desc) == 24
+assert ctypes.sizeof(sl_tune_entry) == 80
 assert ctypes.sizeof(sl_config) == 56
 assert ctypes.sizeof(sl_result) == 72
 RESULT_BYTES = ctypes.sizeof(sl_result)
@@ -118,6 +130,11 @@ PROTOTYPES = {
                         ctypes.POINTER(sl_result)]),
     "sl_run_host": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), ctypes.POINTER(sl_result)]),
     "sl_run_noalloc": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), _P]),
+    "sl_batch_create": (_I32, [ctypes.POINTER(sl_batch_desc), _I32, ctypes.POINTER(sl_tune_entry), _I32,
+                               ctypes.POINTER(ctypes.c_void_p)]),
+    "sl_batch_run": (_I32, [_P, ctypes.POINTER(sl_result), ctypes.POINTER(ctypes.c_uint64)]),
+    "sl_batch_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "sl_batch_destroy": (None, [_P]),
 }
 SL_NOALLOC_MAX_CTAS = 4096
 

@@ -25,53 +25,9 @@
 // in flight into shared memory when the CTA exits.  A consumer warp leaves
 // the ring only when all its lanes agree (__all_sync), so warp-wide shuffles
 // after the loop see every lane.
-#include "sl_device.cuh"
+#include "sl_mbar.cuh"
 
 namespace sl {
-
-constexpr uint32_t WAIT_ITER_CAP = 1u << 26;
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t tx) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-
-// Bounded wait for the phase of `bar` with the given parity to complete.
-// Returns false on timeout (after recording `code`) or when the abort flag is
-// seen (if watch_abort).
-__device__ __forceinline__ bool bounded_wait(uint32_t bar, uint32_t parity, const KArgs& a,
-                                             volatile int* abort_flag, bool watch_abort,
-                                             uint32_t code) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t start = gtimer();
-    for (uint32_t n = 0; n < WAIT_ITER_CAP; ++n) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (watch_abort && *abort_flag) return false;
-        if (gtimer() - start > a.timeout_ns) break;
-    }
-    atomicCAS(a.err, 0u, code);
-    *abort_flag = 1;
-    return false;
-}
 
 template <int DT>
 __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
@@ -93,13 +49,8 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     const uint32_t full0 = smem_addr(full), empty0 = smem_addr(empty);
 
     if (threadIdx.x == 0) {
-        for (uint32_t s = 0; s < nst; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, ncw);
-        }
+        ring_init(full0, empty0, nst, ncw);
         abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
@@ -113,7 +64,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
             c.start(ntiles);
             uint32_t s = 0, r = 0;  // stage and round of chunk i = r*nst + s
             for (uint32_t i = 0; c.it < total; c.next(ntiles), ++i) {
-                if (r > 0 && !bounded_wait(empty0 + 8 * s, (r - 1) & 1u, a, &abort_flag, true,
+                if (r > 0 && !bounded_wait(empty0 + 8 * s, (r - 1) & 1u, a.err, a.timeout_ns, &abort_flag, true,
                                            DEV_ERR_TIMEOUT_EMPTY))
                     break;
                 const uint64_t off = static_cast<uint64_t>(c.tile(a)) * stage_bytes;
@@ -132,8 +83,8 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
             {
                 for (uint32_t s = 0; s < nst; ++s)
                     if (armed & (1u << s))
-                        bounded_wait(full0 + 8 * s, (last_par >> s) & 1u, a, &abort_flag, false,
-                                     DEV_ERR_TIMEOUT_DRAIN);
+                        bounded_wait(full0 + 8 * s, (last_par >> s) & 1u, a.err, a.timeout_ns, &abort_flag,
+                                     false, DEV_ERR_TIMEOUT_DRAIN);
             }
         }
         __syncwarp();
@@ -144,7 +95,8 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
         c.start(ntiles);
         uint32_t s = 0, r = 0;
         for (; c.it < total; c.next(ntiles)) {
-            const bool got = bounded_wait(full0 + 8 * s, r & 1u, a, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
+            const bool got =
+                bounded_wait(full0 + 8 * s, r & 1u, a.err, a.timeout_ns, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
             if (!__all_sync(FULL_MASK, got)) break;  // warp-uniform exit
             const uint64_t off = static_cast<uint64_t>(c.tile(a)) * stage_bytes;
             const uint64_t left = bytes - off;

@@ -13,8 +13,10 @@
  *    equals the sequential stream started from state s.
  *  - uint32 buffer layout: word 2m is the low half and word 2m+1 the high half
  *    of output m, so the little-endian uint64 at word 2m is output m.
- *  - N(0,1) payloads: Box-Muller (1958) on two 53-bit uniforms in (0,1):
- *    normals 2j and 2j+1 come from outputs 2j and 2j+1.
+ *  - N(0,1) payloads: Box-Muller (1958) in single precision on two 24-bit
+ *    uniforms in (0,1) taken from outputs 2j and 2j+1: normal 2j is
+ *    r*cos(theta), normal 2j+1 is r*sin(theta), with r = sqrt(-2 ln u1) and
+ *    theta = 2 pi u2 (|normal| < 5.9).
  *  - Encoders: float32 -> bfloat16 and float32 -> OCP FP8 E4M3, both round to
  *    nearest, ties to even, with E4M3 saturating to +-448.
  *
@@ -61,20 +63,37 @@ static inline double wl_unit(uint64_t v)
     return ((double)(v >> 11) + 0.5) * (1.0 / 9007199254740992.0);
 }
 
-static inline double wl_normal_at(uint64_t seed, uint64_t i)
+static inline float wl_unit24(uint64_t v)
 {
-    uint64_t j = i >> 1;
-    double u1 = wl_unit(wl_splitmix64_at(seed, 2 * j));
-    double u2 = wl_unit(wl_splitmix64_at(seed, 2 * j + 1));
-    double r = sqrt(-2.0 * log(u1));
-    double th = 6.283185307179586476925286766559 * u2;
-    return (i & 1) ? r * sin(th) : r * cos(th);
+    /* (k + 0.5) * 2^-24, k the top 24 bits: strictly inside (0, 1), exact. */
+    return ((float)(uint32_t)(v >> 40) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+/* Normals 2j and 2j+1 of the stream seeded with `seed`. */
+static inline void wl_normal_pair(uint64_t seed, uint64_t j, float *z0, float *z1)
+{
+    float u1 = wl_unit24(wl_splitmix64_at(seed, 2 * j));
+    float u2 = wl_unit24(wl_splitmix64_at(seed, 2 * j + 1));
+    float r = sqrtf(-2.0f * logf(u1));
+    float th = 6.28318530717958647692f * u2;
+    *z0 = r * cosf(th);
+    *z1 = r * sinf(th);
 }
 
 void wl_normal_f32(uint64_t seed, uint64_t first, uint64_t n, float *out)
 {
-    for (uint64_t i = 0; i < n; ++i)
-        out[i] = (float)wl_normal_at(seed, first + i);
+    uint64_t i = 0;
+    while (i < n) {
+        uint64_t g = first + i;
+        float z0, z1;
+        wl_normal_pair(seed, g >> 1, &z0, &z1);
+        if (g & 1) {
+            out[i++] = z1;
+        } else {
+            out[i++] = z0;
+            if (i < n) out[i++] = z1;
+        }
+    }
 }
 
 static inline uint16_t wl_bf16(float f)
@@ -96,36 +115,30 @@ void wl_f32_to_bf16(const float *in, uint64_t n, uint16_t *out)
 
 static inline uint8_t wl_fp8_e4m3(float f)
 {
-    /* Round |f| to the E4M3 grid with ties to even, saturate at 448, encode. */
-    uint8_t sign = signbit(f) ? 0x80 : 0x00;
-    double a = fabs((double)f);
-    if (isnan(f))
-        return (uint8_t)(sign | 0x7F);
-    if (a >= 448.0)
-        return (uint8_t)(sign | 0x7E);
-    /* quantum: 2^-9 below 2^-6 (subnormals), else 2^(e-3) with 2^e <= a. */
-    double q;
-    if (a < 0.015625) {
-        q = 0.001953125;
-    } else {
-        int e;
-        frexp(a, &e);           /* a = f * 2^e, f in [0.5, 1) */
-        q = ldexp(1.0, e - 1 - 3);
+    /* Round to the OCP E4M3 grid with ties to even, saturating at +-448.
+     * Normal range (|f| >= 2^-6): round the binary32 significand from 23 to 3
+     * bits (add half-1 plus the kept LSB, then truncate; a carry moves into
+     * the exponent), rebias 127 -> 7.  Below 2^-6 the grid step is 2^-9:
+     * |f| * 2^9 is exact and nearbyintf rounds it to even (a result of 8 is
+     * the code of 2^-6). */
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    uint8_t sign = (uint8_t)((b >> 24) & 0x80);
+    uint32_t a = b & 0x7FFFFFFFu;
+    if (a > 0x7F800000u)
+        return (uint8_t)(sign | 0x7F);               /* NaN */
+    if (a >= 0x43E00000u)
+        return (uint8_t)(sign | 0x7E);               /* >= 448 (and inf): saturate */
+    if (a < 0x3C800000u) {                           /* below 2^-6 */
+        float mag;
+        memcpy(&mag, &a, 4);
+        return (uint8_t)(sign | (uint8_t)nearbyintf(mag * 512.0f));
     }
-    double r = nearbyint(a / q) * q; /* default rounding mode: ties to even */
-    if (r > 448.0)
-        r = 448.0;
-    if (r == 0.0)
-        return sign;
-    if (r < 0.015625) {
-        int m = (int)(r / 0.001953125); /* 1..7, exact */
-        return (uint8_t)(sign | m);
-    }
-    int e;
-    double fr = frexp(r, &e);        /* r = fr * 2^e, fr in [0.5, 1) */
-    int m = (int)((fr * 2.0 - 1.0) * 8.0); /* exact */
-    int ef = (e - 1) + 7;
-    return (uint8_t)(sign | (ef << 3) | m);
+    uint32_t r = a + 0x7FFFFu + ((a >> 20) & 1u);
+    uint32_t code = (((r >> 23) - 127u + 7u) << 3) | ((r >> 20) & 7u);
+    if (code > 0x7Eu)
+        code = 0x7Eu;
+    return (uint8_t)(sign | code);
 }
 
 void wl_f32_to_fp8_e4m3(const float *in, uint64_t n, float scale, uint8_t *out)
@@ -140,13 +153,21 @@ void wl_f32_to_fp8_e4m3(const float *in, uint64_t n, float scale, uint8_t *out)
 int32_t wl_payload(int32_t dtype, uint64_t seed, uint64_t first, uint64_t n,
                    float scale, void *out)
 {
-    for (uint64_t i = 0; i < n; ++i) {
-        float f = (float)wl_normal_at(seed, first + i);
-        switch (dtype) {
-        case 1: ((float *)out)[i] = f; break;
-        case 2: ((uint16_t *)out)[i] = wl_bf16(f); break;
-        case 3: ((uint8_t *)out)[i] = wl_fp8_e4m3(scale * f); break;
-        default: return -1;
+    if (dtype < 1 || dtype > 3)
+        return -1;
+    uint64_t i = 0;
+    while (i < n) {
+        uint64_t g = first + i;
+        float z[2];
+        wl_normal_pair(seed, g >> 1, &z[0], &z[1]);
+        for (int h = (int)(g & 1); h < 2 && i < n; ++h, ++i) {
+            float f = z[h];
+            if (dtype == 1)
+                ((float *)out)[i] = f;
+            else if (dtype == 2)
+                ((uint16_t *)out)[i] = wl_bf16(f);
+            else
+                ((uint8_t *)out)[i] = wl_fp8_e4m3(scale * f);
         }
     }
     return 0;

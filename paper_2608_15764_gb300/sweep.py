@@ -25,6 +25,9 @@ GPU and checked against the first cell's checksum):
   ncu  a small case for counter captures (1 GiB, one launch per cell, no
        warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), cp.async D=8, TMA
        16 KiB x 2 stages.
+  prec  the precision form: 1 GiB N(0,1) payloads (float32, bfloat16, FP8
+       E4M3 x8) through LDG, cp.async and TMA points; GB/s and the error of
+       the sum against the FP64 oracle.
   ncu-points  every candidate point of the benchmark (tune.default_points)
        on 1 GiB, then LDG K=2 and K=8 on 512 MiB and 2 GiB (one launch each,
        no warm-up): DRAM bytes per launch for the roofline, and the paper's
@@ -194,6 +197,68 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
     return rows
 
 
+PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
+              [dict(mech="cpasync", k=d, cta=256) for d in (2, 4, 6)] +
+              [dict(mech="tma", stage_bytes=sb, stages=n, cta=256) for sb, n in ((16384, 2), (16384, 4), (65536, 2))])
+
+
+def run_prec(out: str | None, repeats: int = 5, gib: float = 1.0, verbose: bool = True):
+    """Precision form: N(0,1) payloads (float32, bfloat16, FP8-E4M3 x8) of
+    `gib` GiB through every mechanism; GB/s and the error of the FP32-Kahan /
+    FP64-combine sum against the FP64 oracle (relative, and normalised by
+    sum|x|), plus the uint32 checksum against the oracle."""
+    import math
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2608_15764_gb300 as sl
+    from . import workloads as wl
+
+    sl.load()
+    rows = []
+    nbytes = int(gib * (1 << 30)) // 16 * 16
+    threads = os.cpu_count() or 1
+    for dt in (wl.F32, wl.BF16, wl.FP8_E4M3):
+        n = nbytes // wl.ELEM_BYTES[dt]
+        host = wl.payload(dt, n)
+        hb = host.view(np.uint8)
+        # reference: the oracle over one contiguous range per thread, the
+        # range sums added with math.fsum (correctly rounded)
+        cut = [i * (n // threads) // 16 * 16 for i in range(threads)] + [n]
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda i: oracle.fsum(dt, host[cut[i]:cut[i + 1]]), range(threads)))
+            cks = list(ex.map(lambda i: oracle.checksum(hb[cut[i] * wl.ELEM_BYTES[dt]:cut[i + 1] * wl.ELEM_BYTES[dt]]),
+                              range(threads)))
+        ref = math.fsum(p[0] for p in parts)
+        absum = math.fsum(p[1] for p in parts)
+        ck = oracle.combine(cks)
+        dev = torch.from_numpy(hb).cuda()
+        cfgs = []
+        for c in PREC_CELLS:
+            kw = {k: v for k, v in c.items() if k != "mech"}
+            cfgs.append(sl.config(c["mech"], **kw))
+        res = sl.sl_sweep(dev, cfgs, dtype=dt, repeats=repeats, warmup=1)
+        for c, rr in zip(PREC_CELLS, res):
+            gbs = [nbytes / r.device_ns for r in rr if r.status == 0 and r.device_ns]
+            fs = [r.fsum for r in rr]
+            row = {"config": "prec", "dtype": {1: "f32", 2: "bf16", 3: "fp8"}[dt], "bytes": nbytes, **c,
+                   "status": rr[0].status, "gbs_median": round(statistics.median(gbs), 2) if gbs else None,
+                   "frac_of_datasheet": round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,
+                   "ref_fsum": ref, "abs_sum": absum,
+                   "rel_err": max(abs(f - ref) for f in fs) / abs(ref),
+                   "err_over_abs_sum": max(abs(f - ref) for f in fs) / absum,
+                   "checksum_ok": all((r.sum_u32, r.xor_u64) == ck for r in rr),
+                   "deterministic": len(set(fs)) == 1}
+            rows.append(row)
+            _emit(out, row, verbose)
+        del dev
+        torch.cuda.empty_cache()
+    return rows
+
+
 def _emit(out, row, verbose):
     if out:
         with open(out, "a") as f:
@@ -223,12 +288,16 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points"])
+                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "prec"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
     a = ap.parse_args(argv)
     t0 = time.time()
+    if a.config == "prec":
+        rows = run_prec(a.out, repeats=a.repeats)
+        print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
+        return 0
     ncu = a.config.startswith("ncu")
     orders = ("asc",) if ncu else tuple(a.orders.split(","))
     rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if ncu else 1)

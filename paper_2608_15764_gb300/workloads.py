@@ -6,7 +6,8 @@ both the CUDA path and the CPU oracle can be fed the same bytes from it.
 * ``splitmix_u32(seed, nwords)`` -- the uint32 buffer: word 2m / 2m+1 are the
   low / high halves of splitmix64 output m (counter form, seed 1 for the
   streaming workloads).
-* ``payload(dtype, seed, n)`` -- N(0,1) float payloads by Box-Muller:
+* ``payload(dtype, seed, n)`` -- N(0,1) float payloads by Box-Muller (single
+  precision, one pair of normals per two splitmix64 outputs):
   float32 (seed 2), bfloat16 = RNE of the float32 (seed 3), FP8 E4M3 = RNE,
   saturating, of 8 x the float32 (seed 4).
 * ``batch_sizes(...)`` -- the 1,024 log-uniform buffer sizes (seed 5) scaled so
@@ -39,7 +40,7 @@ NP_DTYPE = {U32: np.uint32, F32: np.float32, BF16: np.uint16, FP8_E4M3: np.uint8
 DEFAULT_SEED = {U32: 1, F32: 2, BF16: 3, FP8_E4M3: 4}
 FP8_SCALE = 8.0
 SIZES_SEED = 5
-_CHUNK = 1 << 24  # elements per generator call
+_CHUNK = 1 << 22  # elements per generator call (even: chunks start on pair boundaries)
 
 
 def build(force: bool = False) -> str:
