@@ -447,17 +447,24 @@ def run_batch(a):
         ck_ok = ck_ok and all((r.sum_u32, r.xor_u64) == ck for r, ck in zip(plain, cks))
         worst = None
         if dt != wl.U32:
+            # gate per buffer: relative to |exact sum|, or to sum|x| when the
+            # exact sum is small against the payload (|ref| < 1e-3 sum|x| / sqrt(n))
             order = np.argsort(sizes)
             sample = [int(order[i]) for i in np.linspace(0, len(sizes) - 1, 48).astype(int)]
             with ThreadPoolExecutor(threads) as ex:
                 refs = list(ex.map(lambda i: oracle.fsum(dt, hv[offs[i]:offs[i] + sizes[i]]), sample))
-            worst = max(abs(res[i].fsum - ref) / max(abs(ref), 1e-300) for i, (ref, _) in zip(sample, refs))
+            errs = []
+            for i, (ref, absum) in zip(sample, refs):
+                nel = sizes[i] // wl.ELEM_BYTES[dt]
+                small = abs(ref) < 1e-3 * absum / max(nel, 1) ** 0.5
+                errs.append(abs(res[i].fsum - ref) / (absum if small else abs(ref)))
+            worst = max(errs)
         sl.sl_batch_destroy(b)
         per.append({"dtype": name, "bytes": total, "batched_gbs": round(batch_gbs, 1),
                     "batched_ms": round(statistics.median(ts) / 1e6, 4), "per_buffer_gbs": round(plain_gbs, 1),
                     "per_buffer_ms": round(statistics.median(plain_ms), 4),
                     "speedup": round(batch_gbs / plain_gbs, 3), "frac_of_datasheet": round(batch_gbs / DATASHEET_GBS, 4),
-                    "checksums_match_oracle": bool(ck_ok), "fsum_max_rel_err_sample48": worst,
+                    "checksums_match_oracle": bool(ck_ok), "fsum_max_gated_err_sample48": worst,
                     "host_generation_s": round(gen_s, 1),
                     "tuning": [{k: r[k] for k in ("class", "buffers", "bytes", "choice", "gbs")} for r in report]})
     all_bytes = sum(p["bytes"] for p in per)
@@ -469,7 +476,7 @@ def run_batch(a):
                        "l2": "inputs larger than L2; each buffer read once per launch"},
             "per_dtype": per,
             "parity": all(p["checksums_match_oracle"] for p in per) and
-            all(p["fsum_max_rel_err_sample48"] is None or p["fsum_max_rel_err_sample48"] <= 2e-6 for p in per)}
+            all(p["fsum_max_gated_err_sample48"] is None or p["fsum_max_gated_err_sample48"] <= 2e-6 for p in per)}
     print(json.dumps(line), flush=True)
     if a.out:
         with open(a.out, "a") as f:

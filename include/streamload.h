@@ -67,7 +67,12 @@ extern "C" {
 /* ---- enums ------------------------------------------------------------ */
 typedef enum { SL_U32 = 0, SL_F32 = 1, SL_BF16 = 2, SL_FP8_E4M3 = 3 } sl_dtype;
 typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2 } sl_mech;
-typedef enum { SL_ASC = 0, SL_DESC = 1 } sl_order;
+/* Traversal of the buffer by the CTAs.  SL_ASC / SL_DESC: CTA b takes tiles
+ * b, b+grid, ... from the first (or last) tile on (the paper's layout).
+ * SL_DYN (LDG only): CTAs claim contiguous chunks of about 1 MiB from an
+ * atomic counter; integer results are exact, float sums meet the same bound
+ * but are not bit-reproducible between runs. */
+typedef enum { SL_ASC = 0, SL_DESC = 1, SL_DYN = 2 } sl_order;
 /* LDG load flavour: SL_COP_CG is the paper's primary cell (ld.global.cg,
  * §4.2); the other two ask L2 for 256-byte prefetch granules. */
 typedef enum { SL_COP_CG = 0, SL_COP_CG_L2_256 = 1, SL_COP_NC_NA_L2_256 = 2 } sl_cop;
@@ -89,9 +94,8 @@ typedef struct sl_config {
                             32..1024 for LDG/CPASYNC (LDG with K > 8: up to 512);
                             32..992 for TMA, which adds one producer warp. */
     int32_t grid;        /* CTAs; <= 0 selects min(4, resident CTAs per SM) x SMs */
-    int32_t order;       /* sl_order: traversal direction over tiles (ASC walks
-                            tile 0 upward, DESC the last tile downward); never
-                            changes the result */
+    int32_t order;       /* sl_order: traversal of the tiles; never changes the
+                            integer result */
     int32_t flush_l2;    /* nonzero: overwrite a scratch buffer of twice the L2
                             size before the launch, outside the timed interval */
     int32_t passes;      /* read the buffer this many times, >= 1 (0 means 1) */
@@ -262,7 +266,8 @@ int sl_batch_create(const sl_batch_desc* descs, int32_t n, const sl_tune_entry* 
 /* Launch the batch's graph once and wait.  per_buffer (host, n entries, may
  * be NULL to skip the copy-back) receives each buffer's result in descriptor
  * order (device_ns = 0 in each); *total_ns (may be NULL) receives the
- * CUDA-event time of the whole graph launch. */
+ * CUDA-event time of the whole graph launch.  Returns SL_ERR_TIMEOUT if a
+ * bounded device wait gave up during the run (with or without per_buffer). */
 int sl_batch_run(sl_batch* b, sl_result* per_buffer, uint64_t* total_ns);
 
 /* Number of class kernels (graph kernel nodes besides the combine) and the

@@ -66,9 +66,14 @@ def tune(buffers, repeats: int = 3, tie_frac: float = 0.01, verbose: bool = Fals
                 except SLError as e:
                     curve.append({"cand": label(c), "status": e.status})
                     continue
-                sl_batch_run(b, results=False)  # warm-up
-                best_ns = min(sl_batch_run(b, results=False)[1] for _ in range(repeats))
-                sl_batch_destroy(b)
+                try:
+                    sl_batch_run(b, results=False)  # warm-up
+                    best_ns = min(sl_batch_run(b, results=False)[1] for _ in range(repeats))
+                except SLError as e:
+                    curve.append({"cand": label(c), "status": e.status})
+                    continue
+                finally:
+                    sl_batch_destroy(b)
                 curve.append({"cand": label(c), "status": 0, "gbs": nbytes / best_ns, "cfg": c})
             ok = [p for p in curve if p["status"] == 0]
             top = max(p["gbs"] for p in ok)

@@ -39,6 +39,7 @@ constexpr uint64_t HOST_CHUNK = 256ull << 20;     // sl_run_host staging chunk
 constexpr uint64_t TIMEOUT_NS = 2000000000ull;     // per-wait bound, normal runs
 constexpr uint64_t DEBUG_TIMEOUT_NS = 50000000ull;  // per-wait bound, fault-injection runs
 constexpr int64_t MAX_GRID = 1 << 20;
+constexpr uint64_t DYN_CHUNK_VEC = 65536;          // SL_DYN chunk: 1 MiB of 16-byte vectors
 
 thread_local char g_err[1024] = "";
 
@@ -211,7 +212,11 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (bytes > 0 && !buf) return fail(SL_ERR_ARG, "buffer is NULL");
     if ((reinterpret_cast<uintptr_t>(buf) & 15u) != 0) return fail(SL_ERR_ALIGN, "buffer not 16-byte aligned");
     if (cfg->passes < 0) return fail(SL_ERR_ARG, "passes %d < 0", cfg->passes);
-    if (cfg->order != SL_ASC && cfg->order != SL_DESC) return fail(SL_ERR_ARG, "bad order %d", cfg->order);
+    if (cfg->order != SL_ASC && cfg->order != SL_DESC && cfg->order != SL_DYN)
+        return fail(SL_ERR_ARG, "bad order %d", cfg->order);
+    const bool dyn = cfg->order == SL_DYN;
+    if (dyn && (cfg->mech != SL_LDG || cfg->cop != SL_COP_CG))
+        return fail(SL_ERR_ARG, "the SL_DYN traversal is implemented for the LDG mechanism with SL_COP_CG");
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
     const int cta = cfg->cta;
     if (cta < 32 || cta > 1024 || (cta & 31)) return fail(SL_ERR_ARG, "cta %d not a multiple of 32 in 32..1024", cta);
@@ -222,13 +227,17 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     case SL_LDG:
         if (cfg->k < 1 || cfg->k > SL_MAX_K) return fail(SL_ERR_ARG, "LDG K %d not in 1..%d", cfg->k, SL_MAX_K);
         if (cfg->cop < SL_COP_CG || cfg->cop > SL_COP_NC_NA_L2_256) return fail(SL_ERR_ARG, "bad cop %d", cfg->cop);
-        p->fn = sl::ldg_kernel(dtype, cfg->k, cta, cfg->cop);
+        p->fn = dyn ? sl::ldg_dyn_kernel(dtype, cfg->k, cta) : sl::ldg_kernel(dtype, cfg->k, cta, cfg->cop);
+        if (!p->fn && dyn)
+            return fail(SL_ERR_ARG, "no SL_DYN LDG kernel for K %d, cta %d (K in {1,2,3,4,6,8,12,16}, "
+                        "cta 128/256/512)", cfg->k, cta);
         if (!p->fn)
             return fail(SL_ERR_ARG, "no LDG kernel for dtype %d, K %d, cta %d, cop %d (cta must be 32/128/256/512/1024 "
                         "for uint32, 128/256/512 for floats; cop 2 is uint32 only)", dtype, cfg->k, cta, cfg->cop);
         p->block = cta;
         p->smem = 0;
         tile_vec = static_cast<uint64_t>(cta) * cfg->k;
+        if (dyn) tile_vec *= std::max<uint64_t>(1, DYN_CHUNK_VEC / tile_vec);  // chunk of ~1 MiB
         p->warps = cta / 32;
         break;
     case SL_CPASYNC:
@@ -296,6 +305,7 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     a.total = ntiles * passes;
     a.tile_vec = static_cast<uint32_t>(tile_vec);
     a.desc = cfg->order == SL_DESC ? 1 : 0;
+    a.next = nullptr;  // set by the caller for SL_DYN
     a.nst = cfg->mech == SL_TMA ? cfg->stages : 0;
     a.debug = cfg->debug_flags;
     a.timeout_ns = cfg->debug_flags ? DEBUG_TIMEOUT_NS : TIMEOUT_NS;
@@ -331,6 +341,7 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
     p.args.err = sl::ctrl_err(c->err);
     p.args.done = sl::ctrl_done(c->err);
     p.args.result = dev_out;  // the kernel's last CTA writes the result
+    if (cfg->order == SL_DYN) p.args.next = sl::ctrl_next(c->err);
     if (cfg->flush_l2) CUDA_TRY(sl::launch_flush(c->flush, c->flush_bytes / 16, c->info.sm_count, s));
     if (events) CUDA_TRY(cudaEventRecord(c->ev0, s));
     rc = launch(p, s);
@@ -516,10 +527,16 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
         a.err = c->err;
         a.result = nullptr;  // combined over all chunks below
         a.done = nullptr;
+        if (cfg->order == SL_DYN) {  // no last-CTA reset here: clear the chunk counter per launch
+            a.next = sl::ctrl_next(c->err);
+            CUDA_TRY(cudaMemsetAsync(a.next, 0, sizeof(uint32_t), s));
+        }
         void* args[] = {&a};
         CUDA_TRY(cudaLaunchKernel(p.fn, dim3(static_cast<unsigned>(p.grid)), dim3(p.block), args, p.smem, s));
         CUDA_TRY(cudaEventRecord(c->consumed[b], s));
     }
+    if (cfg->order == SL_DYN)  // leave the chunk counter at zero for the next launch
+        CUDA_TRY(cudaMemsetAsync(sl::ctrl_next(c->err), 0, sizeof(uint32_t), s));
     CUDA_TRY(sl::launch_combine(c->parts, per_parts * nchunks, sl::ctrl_window(c->err), c->err, c->dres, s));
     CUDA_TRY(cudaMemcpyAsync(c->hres, c->dres, sizeof(sl_result), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaEventRecord(c->ev1, s));

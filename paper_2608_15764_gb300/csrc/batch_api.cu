@@ -71,6 +71,7 @@ struct sl_batch {
     uint32_t* d_ctrl = nullptr;  // [0]: error word; [16 + g]: item counter of group g
     size_t ctrl_bytes = 0;
     sl_result* h_results = nullptr;
+    uint32_t* h_err = nullptr;   // pinned copy of the error word after each run
     cudaStream_t stream = nullptr;
     std::vector<cudaStream_t> branch;
     std::vector<cudaEvent_t> branch_ev;
@@ -97,6 +98,7 @@ void release(sl_batch* b) {
     cudaFree(b->d_results);
     cudaFree(b->d_ctrl);
     cudaFreeHost(b->h_results);
+    cudaFreeHost(b->h_err);
     (void)cudaGetLastError();
     delete b;
 }
@@ -214,6 +216,7 @@ int build_batch(sl_batch* b, const sl_batch_desc* descs, int32_t n, const sl_tun
     B_TRY(cudaMalloc(&b->d_results, std::max<size_t>(n, 1) * sizeof(sl_result)), "cudaMalloc failed");
     B_TRY(cudaMalloc(&b->d_ctrl, b->ctrl_bytes), "cudaMalloc failed");
     B_TRY(cudaMallocHost(&b->h_results, std::max<size_t>(n, 1) * sizeof(sl_result)), "cudaMallocHost failed");
+    B_TRY(cudaMallocHost(&b->h_err, sizeof(uint32_t)), "cudaMallocHost failed");
     if (!all.empty())
         B_TRY(cudaMemcpy(b->d_items, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice), "copy failed");
     if (n > 0) B_TRY(cudaMemcpy(b->d_segs, segs.data(), n * sizeof(BufSeg), cudaMemcpyHostToDevice), "copy failed");
@@ -306,11 +309,13 @@ int sl_batch_run(sl_batch* b, sl_result* per_buffer, uint64_t* total_ns) {
     if (per_buffer && b->n > 0)
         B_TRY(cudaMemcpyAsync(b->h_results, b->d_results, b->n * sizeof(sl_result), cudaMemcpyDeviceToHost, b->stream),
               "result copy failed");
+    B_TRY(cudaMemcpyAsync(b->h_err, b->d_ctrl, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->stream),
+          "error-word copy failed");
     B_TRY(cudaStreamSynchronize(b->stream), "batch run failed");
     float ms = 0.0f;
     B_TRY(cudaEventElapsedTime(&ms, b->e0, b->e1), "event timing failed");
     if (total_ns) *total_ns = static_cast<uint64_t>(static_cast<double>(ms) * 1e6 + 0.5);
-    int st = SL_OK;
+    int st = *b->h_err ? SL_ERR_TIMEOUT : SL_OK;
     if (per_buffer && b->n > 0) {
         std::memcpy(per_buffer, b->h_results, b->n * sizeof(sl_result));
         for (int i = 0; i < b->n; ++i)

@@ -112,6 +112,10 @@ __global__ void __launch_bounds__(1024) kb_tma(const BArgs a) {
                         break;
                     }
                     if (done) {
+                        // The copy this stage last carried has landed (its
+                        // consumers released the stage), and the sentinel
+                        // advances full[s] by one more phase: stop draining it.
+                        armed &= ~(1u << s);
                         meta[s] = StageMeta{0u, 0u, STAGE_DONE, 0u};
                         mbar_arrive(full0 + 8 * s);
                     } else {

@@ -66,6 +66,70 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
     cta_finish<DT>(acc, true, threadIdx.x >> 5, CTA / 32, a);
 }
 
+// SL_DYN traversal: CTAs claim contiguous chunks of a.tile_vec vectors (a
+// multiple of CTA*K, about 1 MiB) from the counter *a.next, so each CTA
+// streams long contiguous runs and faster CTAs take more chunks.  Within a
+// chunk the tiles and loads are those of k_ldg (K independent 16-byte loads
+// per thread per tile, guarded ragged tail).  Thread 0 claims the following
+// chunk while the CTA works on the current one (one CTA barrier per chunk).
+// Integer results are exact; float sums are correct to the same bound but not
+// bit-reproducible between runs, since a CTA's partial covers whichever
+// chunks it claimed.
+template <int K, int CTA, int DT>
+__global__ void __launch_bounds__(CTA, 1) k_ldg_dyn(const KArgs a) {
+    constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
+    __shared__ uint32_t slot[2];
+    cta_start(a);
+    const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
+    const uint32_t chunk_vec = a.tile_vec;
+    const uint32_t nchunks = static_cast<uint32_t>(a.ntiles);
+    const uint32_t total = static_cast<uint32_t>(a.total);
+    Acc<DT> acc;
+    uint32_t full_iters = 0;
+    volatile uint32_t* vslot = slot;
+    if (threadIdx.x == 0) vslot[0] = atomicAdd(a.next, 1u);
+    __syncthreads();
+    uint32_t cur = vslot[0];
+#pragma unroll 1
+    for (uint32_t j = 0; cur < total; ++j) {
+        if (threadIdx.x == 0) vslot[(j + 1) & 1] = atomicAdd(a.next, 1u);
+        const uint64_t base = static_cast<uint64_t>(cur % nchunks) * chunk_vec;
+        const uint64_t left = a.nvec - base;
+        const uint32_t len = left < chunk_vec ? static_cast<uint32_t>(left) : chunk_vec;
+        const uint4* p = buf + base + threadIdx.x;
+        const uint32_t nfull = len / TILE;
+#pragma unroll 1
+        for (uint32_t t = 0; t < nfull; ++t, p += TILE) {
+            uint4 v[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = ldg16<SL_COP_CG>(p + k * CTA);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc.fold(v[k]);
+        }
+        full_iters += nfull;
+        const uint32_t rem = len - nfull * TILE;
+        if (rem) {
+            uint4 v[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (threadIdx.x + k * CTA < rem) v[k] = ldg16<SL_COP_CG>(p + k * CTA);
+                else v[k] = make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (threadIdx.x + k * CTA < rem) {
+                    acc.fold(v[k]);
+                    acc.n += 1;
+                }
+            }
+        }
+        __syncthreads();  // the prefetched claim is visible; the slot read next is not rewritten until j+2
+        cur = vslot[(j + 1) & 1];
+    }
+    acc.n += full_iters * K;
+    cta_finish<DT>(acc, true, threadIdx.x >> 5, CTA / 32, a);
+}
+
 }  // namespace sl
 
 // Table of instantiations K = 1..16 x CTA sizes x load flavours for one dtype.

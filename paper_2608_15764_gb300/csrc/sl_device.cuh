@@ -175,7 +175,8 @@ __device__ __forceinline__ void warp_merge(uint32_t& s, uint64_t& x, uint64_t& n
 // and the per-warp results are merged by fixed shuffle butterflies, so the
 // float sum has a fixed order for a given launch shape.  Integer parts are
 // exact.  The device error word becomes the status and is cleared; the CTA
-// counter and the timing window are reset for the next launch.
+// counter, the chunk counter (if any) and the timing window are reset for the
+// next launch.
 template <typename T, typename Op>
 __device__ __forceinline__ T warp_all(T v, Op op) {
 #pragma unroll
@@ -241,6 +242,7 @@ __device__ __forceinline__ void final_combine(const KArgs& a) {
         r->smem_bytes = 0;
         *a.err = 0;
         *a.done = 0;
+        if (a.next) *a.next = 0;
         w[0] = ~0ull;
         w[1] = 0;
     }

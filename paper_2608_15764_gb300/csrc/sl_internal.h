@@ -41,6 +41,8 @@ struct KArgs {
                             // partials into *result (else a separate combine)
     uint32_t* done;         // CTAs finished (zero before the launch; the last
                             // CTA resets it)
+    uint32_t* next;         // SL_DYN traversal: next chunk to claim (zero before
+                            // the launch; the last CTA resets it), else NULL
 };
 
 // Device error codes written to *err (first writer wins).
@@ -50,6 +52,7 @@ enum : uint32_t { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT_FULL = 1, DEV_ERR_TIMEOUT_EM
 // Kernel lookup.  Each returns the __global__ function for the given
 // instantiation, or nullptr when out of range.  All take (KArgs).
 const void* ldg_kernel(int dtype, int k, int cta, int cop);
+const void* ldg_dyn_kernel(int dtype, int k, int cta);
 const void* cpasync_kernel(int dtype, int d);
 const void* tma_kernel(int dtype);
 
@@ -63,10 +66,12 @@ cudaError_t launch_combine(const WarpPartial* parts, uint64_t nparts, uint64_t* 
                            sl_result* out, cudaStream_t s);
 
 // Layout of the 256-byte control block shared by a launch and its combine:
-// error word at byte 0, finished-CTA counter at byte 64, window at byte 128.
+// error word at byte 0, finished-CTA counter at byte 64, window at byte 128,
+// chunk counter of the SL_DYN traversal at byte 192.
 constexpr int CTRL_BYTES = 256;
 inline uint32_t* ctrl_err(void* c) { return static_cast<uint32_t*>(c); }
 inline uint32_t* ctrl_done(void* c) { return static_cast<uint32_t*>(c) + 16; }
 inline uint64_t* ctrl_window(void* c) { return static_cast<uint64_t*>(c) + 16; }
+inline uint32_t* ctrl_next(void* c) { return static_cast<uint32_t*>(c) + 48; }
 
 }  // namespace sl

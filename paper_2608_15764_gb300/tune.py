@@ -28,6 +28,7 @@ class Point:
     stage_bytes: int = 0  # TMA
     stages: int = 0       # TMA
     cop: int = 0
+    order: int = 0        # SL_ASC, or SL_DYN (dynamic contiguous chunks, LDG)
     gbs: list = field(default_factory=list)  # per repeat
     window_gbs: list = field(default_factory=list)
     status: int = SL_OK
@@ -38,6 +39,8 @@ class Point:
         if self.mech == SL_TMA:
             return config(self.mech, cta=self.cta, grid=self.grid, stage_bytes=self.stage_bytes,
                           stages=self.stages, **kw)
+        if self.order and "order" not in kw:
+            kw["order"] = self.order
         return config(self.mech, k=self.k, cta=self.cta, grid=self.grid, cop=self.cop, **kw)
 
     @property
@@ -54,7 +57,8 @@ class Point:
     def label(self) -> str:
         if self.mech == SL_TMA:
             return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}"
-        return f"{MECH_NAMES[self.mech]} {'K' if self.mech == SL_LDG else 'D'}={self.k} cta={self.cta} cop={self.cop}"
+        dyn = " dyn" if self.order == 2 else ""
+        return f"{MECH_NAMES[self.mech]} {'K' if self.mech == SL_LDG else 'D'}={self.k} cta={self.cta} cop={self.cop}{dyn}"
 
     def as_dict(self) -> dict:
         d = {"mech": MECH_NAMES[self.mech], "cta": self.cta, "grid": self.grid_used, "status": self.status,
@@ -63,13 +67,15 @@ class Point:
         if self.mech == SL_TMA:
             d.update(stage_bytes=self.stage_bytes, stages=self.stages)
         else:
-            d.update(k=self.k, cop=self.cop)
+            d.update(k=self.k, cop=self.cop, order=self.order)
         return d
 
 
 def parse_point(text: str) -> Point:
-    """'ldg:K:cta[:cop]', 'cpasync:D:cta' or 'tma:stage_bytes:stages:cta'."""
+    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'cpasync:D:cta' or 'tma:stage_bytes:stages:cta'."""
     f = text.split(":")
+    if f[0] == "ldgdyn":
+        return Point(SL_LDG, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256, order=2)
     mech = f[0]
     if mech == "tma":
         return Point(SL_TMA, stage_bytes=int(f[1]), stages=int(f[2]), cta=int(f[3]) if len(f) > 3 else 256)
@@ -82,6 +88,8 @@ def parse_point(text: str) -> Point:
 def default_points(cta: int = 256) -> list[Point]:
     pts = [Point(SL_LDG, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8, 12, 16)]
     pts += [Point(SL_LDG, k=k, cta=cta, cop=1) for k in (1, 2, 4, 8)]
+    pts += [Point(SL_LDG, k=k, cta=cta, order=2) for k in (2, 3, 4, 6, 8)]
+    pts += [Point(SL_LDG, k=k, cta=512, order=2) for k in (2, 4)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in (1, 2, 4, 8)]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n)
             for s in (4096, 16384, 65536) for n in (2, 4, 8) if s * n <= 227 * 1024]

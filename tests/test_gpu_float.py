@@ -70,6 +70,13 @@ def test_ldg_float(sl, payloads, dt, k, cta):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_ldg_dynamic_float(sl, payloads, dt, k):
+    for _ in range(2):
+        _check(sl, payloads[dt], dt, sl.config("ldg", k=k, cta=256, order="dyn"))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("d", [1, 2, 4, 8])
 def test_cpasync_float(sl, payloads, dt, d):
     _check(sl, payloads[dt], dt, sl.config("cpasync", k=d, cta=256))

@@ -118,6 +118,36 @@ def test_small_and_ragged(sl, data, nvec, mech, kw):
     _check(sl, dev, nbytes, want, sl.config(mech, cta=256, **kw))
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8, 12, 16])
+@pytest.mark.parametrize("cta", [128, 256, 512])
+def test_ldg_dynamic_chunks(sl, data, k, cta):
+    """SL_DYN: CTAs claim ~1 MiB contiguous chunks from a counter; the counter
+    is reset by the last CTA, so back-to-back launches all cover the buffer
+    exactly once."""
+    dev, _, want = data
+    for grid in (0, 5):
+        for _ in range(2):
+            r = _check(sl, dev, NBYTES, want, sl.config("ldg", k=k, cta=cta, grid=grid, order="dyn"))
+    _check(sl, dev, NBYTES, ((3 * want[0]) % (1 << 32), want[1]),
+           sl.config("ldg", k=k, cta=cta, order="dyn", passes=3), passes=3)
+
+
+@pytest.mark.parametrize("nvec", [0, 1, 33, 4096 + 5, 65536, 65536 + 17, 3 * 65536 + 1])
+def test_ldg_dynamic_ragged(sl, data, nvec):
+    dev, host, _ = data
+    nbytes = 16 * nvec
+    _check(sl, dev, nbytes, oracle.checksum(host[: nbytes // 4]), sl.config("ldg", k=4, cta=256, order="dyn"))
+
+
+def test_dynamic_rejected_outside_ldg(sl, data):
+    dev, _, _ = data
+    for cfg in [sl.config("tma", order="dyn"), sl.config("cpasync", order="dyn"),
+                sl.config("ldg", k=5, order="dyn"), sl.config("ldg", k=2, cop=1, order="dyn")]:
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_run(dev, dtype=sl.SL_U32, cfg=cfg)
+        assert e.value.status == sl.SL_ERR_ARG
+
+
 def test_empty_buffer(sl):
     r = sl.sl_run(0, nbytes=0, dtype=sl.SL_U32, cfg=sl.config("ldg", k=2))
     assert (r.sum_u32, r.xor_u64, r.issued_loads, r.grid) == (0, 0, 0, 0)
@@ -196,7 +226,8 @@ def test_enqueue_many_on_one_stream(sl, data):
         assert r.issued_loads == NBYTES // 16
 
 
-@pytest.mark.parametrize("mech,kw", [("ldg", {"k": 4}), ("tma", {"stage_bytes": 16384, "stages": 4})])
+@pytest.mark.parametrize("mech,kw", [("ldg", {"k": 4}), ("tma", {"stage_bytes": 16384, "stages": 4}),
+                                     ("ldg", {"k": 4, "order": "dyn"})])
 def test_run_host_matches(sl, data, mech, kw):
     _, host, want = data
     pinned = torch.from_numpy(host.view(np.uint8)).pin_memory()
