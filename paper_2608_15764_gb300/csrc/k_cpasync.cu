@@ -3,11 +3,11 @@
 // Paper §4.3 compares cp.async, which writes shared memory without a
 // destination register, against plain loads at equal offered concurrency.
 // Here each thread copies 16 bytes per commit group with
-// cp.async.cg.shared.global into stage slot g mod D of a D-deep ring and keeps
-// D groups in flight: after committing group g+D-1 it waits until at most D-1
-// groups are pending (so group g has landed), reads its own slot back with
-// ld.shared and folds it.  A thread reads only the slot it wrote itself, so no
-// CTA barrier is needed.
+// cp.async.cg.shared.global into a D-slot ring and keeps D groups in flight:
+// it waits until at most D-1 groups are pending (so the oldest has landed),
+// reads that slot back with ld.shared and folds it, then refills the slot
+// with the matching chunk of its next tile and commits.  A thread reads only
+// the slot it wrote itself, so no CTA barrier is needed.
 //
 // The address sequence of a thread is the LDG kernel's at K = D: tile = cta*D
 // vectors, CTA b walks tiles b, b+grid, ..., and chunk k of a tile is vector
@@ -23,64 +23,59 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Position in the chunk sequence of one CTA.
-struct ChunkCursor {
-    TileCursor c;
-    uint32_t k;
-    __device__ __forceinline__ void start(uint32_t ntiles) { c.start(ntiles); k = 0; }
-    template <int D>
-    __device__ __forceinline__ void next(uint32_t ntiles) {
-        if (++k == D) { k = 0; c.next(ntiles); }
-    }
-    // vector index of this thread's chunk, or ~0 when past the end
-    __device__ __forceinline__ uint64_t vec(const KArgs& a, uint32_t total, uint32_t cta) const {
-        if (c.it >= total) return ~0ull;
-        const uint64_t idx = static_cast<uint64_t>(c.tile(a)) * a.tile_vec + k * cta + threadIdx.x;
-        return idx < a.nvec ? idx : ~0ull;
-    }
-};
-
 template <int D, int DT>
 __global__ void __launch_bounds__(1024) k_cpasync(const KArgs a) {
-    extern __shared__ __align__(16) uint4 ring[];  // [D][cta]
+    extern __shared__ __align__(16) uint4 ring[];  // [D][cta]: slot k holds chunk k of a tile
     cta_start(a);
     const uint32_t cta = blockDim.x;
+    const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
     const uint32_t ntiles = static_cast<uint32_t>(a.ntiles);
     const uint32_t total = static_cast<uint32_t>(a.total);
-    const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
-    const uint32_t my_slot0 = smem_addr(ring + threadIdx.x);
-    const uint32_t slot_stride = cta * 16u;
+    const uint64_t nvec = a.nvec;
+    const uint64_t tile_vec = static_cast<uint64_t>(cta) * D;
+    const uint32_t my0 = smem_addr(ring + threadIdx.x), stride = cta * 16u;
     Acc<DT> acc;
-    ChunkCursor ic, cc;  // issue and consume cursors
-    ic.start(ntiles);
-    cc.start(ntiles);
-    uint32_t islot = 0, cslot = 0;
-
+    uint32_t full_tiles = 0;
+    TileCursor c;
+    c.start(ntiles);
+    if (c.it < total) {
+        // prologue: the D chunks of the first tile, one commit group each
+        const uint64_t base = static_cast<uint64_t>(c.tile(a)) * tile_vec + threadIdx.x;
 #pragma unroll
-    for (int g = 0; g < D - 1; ++g) {
-        const uint64_t idx = ic.vec(a, total, cta);
-        if (idx != ~0ull) cp_async16(my_slot0 + islot * slot_stride, buf + idx);
-        cp_async_commit();
-        ic.next<D>(ntiles);
-        islot = (islot + 1 == D) ? 0 : islot + 1;
+        for (int k = 0; k < D; ++k) {
+            if (base + static_cast<uint64_t>(k) * cta < nvec) cp_async16(my0 + k * stride, buf + base + k * cta);
+            cp_async_commit();
+        }
     }
 #pragma unroll 1
-    while (cc.c.it < total) {
-        const uint64_t idx = ic.vec(a, total, cta);
-        if (idx != ~0ull) cp_async16(my_slot0 + islot * slot_stride, buf + idx);
-        cp_async_commit();
-        ic.next<D>(ntiles);
-        islot = (islot + 1 == D) ? 0 : islot + 1;
-
-        cp_async_wait<D - 1>();
-        if (cc.vec(a, total, cta) != ~0ull) {
-            acc.fold(lds16(my_slot0 + cslot * slot_stride));
-            acc.n += 1;
+    while (c.it < total) {
+        const uint32_t cur = c.tile(a);
+        c.next(ntiles);
+        const bool has_next = c.it < total;
+        const uint32_t nxt = has_next ? c.tile(a) : 0u;
+        const uint64_t cbase = static_cast<uint64_t>(cur) * tile_vec;
+        const uint64_t nbase = static_cast<uint64_t>(nxt) * tile_vec;
+        const bool cfull = cbase + tile_vec <= nvec;
+        const bool nfull = has_next && nbase + tile_vec <= nvec;
+        const uint4* np = buf + nbase + threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            // D groups are pending; wait until the oldest (chunk k of cur) has landed
+            cp_async_wait<D - 1>();
+            const uint64_t cv = cbase + static_cast<uint64_t>(k) * cta + threadIdx.x;
+            if (cfull || cv < nvec) {
+                acc.fold(lds16(my0 + k * stride));
+                if (!cfull) acc.n += 1;
+            }
+            // refill slot k with chunk k of the next tile (an empty group at the end)
+            if (nfull || (has_next && nbase + static_cast<uint64_t>(k) * cta + threadIdx.x < nvec))
+                cp_async16(my0 + k * stride, np + k * cta);
+            cp_async_commit();
         }
-        cc.next<D>(ntiles);
-        cslot = (cslot + 1 == D) ? 0 : cslot + 1;
+        if (cfull) ++full_tiles;
     }
     cp_async_wait<0>();
+    acc.n += full_tiles * D;
     cta_finish<DT>(acc, true, threadIdx.x >> 5, cta >> 5, a);
 }
 

@@ -13,7 +13,9 @@ GPU and checked against the first cell's checksum):
   c2   4 GiB; LDG K in {1,2,3,4,6,8,12,16} x CTA {128,256,512} x resident
        CTAs per SM r = 1..8 (grid = r x SMs; a cell is infeasible when the
        occupancy API allows fewer than r) x sweep order {asc, desc}.
-  c3   4 GiB; same bytes through LDG K 1..16, cp.async D 1..8 and TMA
+  c3   4 GiB; same bytes through LDG K 1..16 (grid-stride tiles, and the
+       dynamic contiguous-chunk traversal for K in {1,2,3,4,6,8,12,16}),
+       cp.async D 1..8 and TMA
        stage {4,16,64} KiB x stages 2..8 (cells over the shared-memory limit
        are recorded as infeasible).
   c4   allocations 512 MiB, 1, 2, 4, 8, 16, 20 GiB; LDG K in {1,2,4,8,16}.
@@ -69,6 +71,8 @@ def _cells(config: str, sms: int):
     elif config == "c3":
         for k in range(1, 17):
             yield dict(mech="ldg", k=k, cta=256, grid=0, gib=4)
+        for k in (1, 2, 3, 4, 6, 8, 12, 16):
+            yield dict(mech="ldg", k=k, cta=256, grid=0, trav=2, gib=4)
         for d in range(1, 9):
             yield dict(mech="cpasync", k=d, cta=256, grid=0, gib=4)
         for sb in (4096, 16384, 65536):
@@ -92,7 +96,8 @@ def _cells(config: str, sms: int):
             if p.mech == 2:
                 yield dict(mech="tma", stage_bytes=p.stage_bytes, stages=p.stages, cta=p.cta, grid=0, gib=1)
             else:
-                yield dict(mech="ldg" if p.mech == 0 else "cpasync", k=p.k, cta=p.cta, grid=0, cop=p.cop, gib=1)
+                yield dict(mech="ldg" if p.mech == 0 else "cpasync", k=p.k, cta=p.cta, grid=0, cop=p.cop,
+                           trav=p.order, gib=1)
         for gib in (0.5, 2):
             for k in (2, 8):
                 yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
@@ -149,7 +154,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                 if c["mech"] == "tma":
                     cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
                 else:
-                    cfg = sl.config(c["mech"], k=c["k"], cop=c.get("cop", 0), **kw)
+                    cfg = sl.config(c["mech"], k=c["k"], cop=c.get("cop", 0), order=c.get("trav", 0), **kw)
                 status, resident = 0, 0
                 try:
                     plan = sl.sl_plan(nbytes, sl.SL_U32, cfg)

@@ -34,7 +34,9 @@ def test_cell_grids():
     assert {c["grid"] for c in c2} == {r * sms for r in range(1, 9)}
     assert {c["k"] for c in c2} == {1, 2, 3, 4, 6, 8, 12, 16}
     c3 = list(sweep._cells("c3", sms))
-    assert sum(c["mech"] == "ldg" for c in c3) == 16 and sum(c["mech"] == "cpasync" for c in c3) == 8
+    assert sum(c["mech"] == "ldg" and not c.get("trav") for c in c3) == 16
+    assert sum(c["mech"] == "ldg" and c.get("trav") == 2 for c in c3) == 8
+    assert sum(c["mech"] == "cpasync" for c in c3) == 8
     assert sum(c["mech"] == "tma" for c in c3) == 21
     c4 = list(sweep._cells("c4", sms))
     assert sorted({c["gib"] for c in c4}) == [0.5, 1, 2, 4, 8, 16, 20]
