@@ -113,24 +113,36 @@ __device__ __forceinline__ float vec_sum(const uint4& v) {
 // ---- the fold ----------------------------------------------------------------
 // Per-thread accumulator.  Integer part (every dtype): wraparound uint32 sum
 // of the four words and XOR of the two little-endian uint64 halves.  Float
-// part (float dtypes): FP32 Kahan summation of the per-vector sums; the
-// represented value is ks - kc.
+// part: FP32 Kahan summation; the represented value is ks - kc.  FP32
+// payloads feed every element to the compensated sum (an uncompensated
+// 4-element partial sum would carry about u*|x| of rounding per vector, which
+// dominates when a buffer's exact sum nearly cancels).  BF16 and FP8 payloads
+// feed per-vector sums: exact for FP8 (see vec_sum_fp8), and for BF16 exact
+// unless the eight values span more than 16 binades.
 template <int DT>
 struct Acc {
     uint32_t s = 0, xl = 0, xh = 0;
     uint32_t n = 0;  // 16-byte loads folded by this thread (the host keeps it below 2^32)
     float ks = 0.0f, kc = 0.0f;
 
+    __device__ __forceinline__ void kahan(float p) {
+        const float y = p - kc;
+        const float t = ks + y;
+        kc = (t - ks) - y;
+        ks = t;
+    }
+
     __device__ __forceinline__ void fold(const uint4& v) {
         s += (v.x + v.y) + (v.z + v.w);
         xl ^= v.x ^ v.z;
         xh ^= v.y ^ v.w;
-        if constexpr (DT != SL_U32) {
-            const float p = vec_sum<DT>(v);
-            const float y = p - kc;
-            const float t = ks + y;
-            kc = (t - ks) - y;
-            ks = t;
+        if constexpr (DT == SL_F32) {
+            kahan(__uint_as_float(v.x));
+            kahan(__uint_as_float(v.y));
+            kahan(__uint_as_float(v.z));
+            kahan(__uint_as_float(v.w));
+        } else if constexpr (DT != SL_U32) {
+            kahan(vec_sum<DT>(v));
         }
     }
 };

@@ -25,8 +25,8 @@ GPU and checked against the first cell's checksum):
   primary  the paper's primary cell shape (§4.2: one CTA of 32 warps per SM,
        .cg, 16-byte loads), K in {1,2,4,8}, on 4 GiB.
   ncu  a small case for counter captures (1 GiB, one launch per cell, no
-       warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), cp.async D=8, TMA
-       16 KiB x 2 stages.
+       warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), LDG K=4 with the
+       dynamic-chunk traversal, cp.async D=2, TMA 16 KiB x 2 stages.
   prec  the precision form: 1 GiB N(0,1) payloads (float32, bfloat16, FP8
        E4M3 x8) through LDG, cp.async and TMA points; GB/s and the error of
        the sum against the FP64 oracle.
@@ -104,7 +104,8 @@ def _cells(config: str, sms: int):
     elif config == "ncu":
         yield dict(mech="ldg", k=2, cta=256, grid=4 * sms, gib=1)
         yield dict(mech="ldg", k=8, cta=256, grid=4 * sms, gib=1)
-        yield dict(mech="cpasync", k=8, cta=256, grid=0, gib=1)
+        yield dict(mech="ldg", k=4, cta=256, grid=0, trav=2, gib=1)
+        yield dict(mech="cpasync", k=2, cta=256, grid=0, gib=1)
         yield dict(mech="tma", stage_bytes=16384, stages=2, cta=256, grid=0, gib=1)
     else:
         raise ValueError(config)

@@ -1,13 +1,9 @@
 """Timing audit of the offered-ILP axis (replaces the paper's SASS audit,
 §3 "Instruments"): a lone warp reading from HBM (L2 flushed before each run)
-is latency-bound, so if a thread really keeps its K loads in flight the time
-of a fixed-work pass falls about K-fold; if the loads were serialized behind
-their consumers it would stay flat.
-
-cp.async: one warp gains clearly from a second commit group in flight but
-then reaches a floor of roughly 160 ns per group on GB300 (measured; the
-per-group cost of commit/wait/read-back, not the memory latency), so the
-check there is that depth overlaps groups and never hurts."""
+is latency-bound, so if a thread really keeps its K loads (LDG) or D commit
+groups (cp.async) in flight, the time of a fixed-work pass falls about
+K-fold; if the loads were serialized behind their consumers it would stay
+flat."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -49,9 +45,8 @@ def test_lone_warp_ldg_time_scales_with_k(sl, buf):
         assert speedup >= 0.5 * k, (k, speedup, t)
 
 
-def test_lone_warp_cpasync_groups_overlap(sl, buf):
+def test_lone_warp_cpasync_time_scales_with_depth(sl, buf):
     ds = [1, 2, 4, 8]
     t = {d: _time(sl, buf, sl.config("cpasync", k=d, cta=32, grid=1, flush_l2=True)) for d in ds}
-    assert t[1] / t[2] >= 1.4, t
-    for a, b in zip(ds, ds[1:]):
-        assert t[b] <= 1.05 * t[a], t
+    for d in ds[1:]:
+        assert t[1] / t[d] >= 0.5 * d, (d, t)
