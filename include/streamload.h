@@ -22,7 +22,8 @@
  *               library's design).
  *
  * and two layered forms: float payloads (FP32 / BF16 / FP8-E4M3) summed with
- * FP32 Kahan accumulation and an FP64 final combine, and a batched form (many
+ * compensated FP32 accumulation (every addition's rounding error recovered
+ * with TwoSum) and an FP64 final combine, and a batched form (many
  * buffers, one CUDA-graph launch) declared further below.
  *
  * Conventions for every function:
@@ -186,9 +187,11 @@ int sl_plan(uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out)
  * K); load k of thread t reads vector tile*cta*K + k*cta + t; the last tile is
  * guarded so that issued loads = passes*bytes/16 exactly at every K.  TMA
  * walks stage-sized chunks the same way.  dtype selects the fold: SL_U32
- * computes sum_u32 / xor_u64; float dtypes also compute fsum (per-thread FP32
- * Kahan over per-vector sums, warp TwoSum, FP64 combine of per-warp
- * partials).  Synchronous: returns after the result is on the host. */
+ * computes sum_u32 / xor_u64; float dtypes also compute fsum (per-thread
+ * compensated FP32 sum -- FP32: every element, BF16/FP8: per-vector sums --
+ * with each addition's error recovered by TwoSum, double-float merges of
+ * warps and CTAs, FP64 combine of per-CTA partials).  Synchronous: returns
+ * after the result is on the host. */
 int sl_run(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
            sl_result* out);
 

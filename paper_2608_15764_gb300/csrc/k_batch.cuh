@@ -51,7 +51,7 @@ template <int DT>
 __device__ __forceinline__ void warp_item_store(const Acc<DT>& acc, WarpPartial* dst) {
     uint32_t s = acc.s;
     uint64_t x = (static_cast<uint64_t>(acc.xh) << 32) | acc.xl, n = acc.n;
-    float hi = acc.ks, lo = -acc.kc;
+    float hi = acc.fs, lo = acc.fe;
     warp_merge<DT>(s, x, n, hi, lo);
     if ((threadIdx.x & 31) == 0) {
         WarpPartial p;

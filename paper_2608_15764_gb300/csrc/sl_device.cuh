@@ -113,23 +113,24 @@ __device__ __forceinline__ float vec_sum(const uint4& v) {
 // ---- the fold ----------------------------------------------------------------
 // Per-thread accumulator.  Integer part (every dtype): wraparound uint32 sum
 // of the four words and XOR of the two little-endian uint64 halves.  Float
-// part: FP32 Kahan summation; the represented value is ks - kc.  FP32
-// payloads feed every element to the compensated sum (an uncompensated
-// 4-element partial sum would carry about u*|x| of rounding per vector, which
-// dominates when a buffer's exact sum nearly cancels).  BF16 and FP8 payloads
-// feed per-vector sums: exact for FP8 (see vec_sum_fp8), and for BF16 exact
-// unless the eight values span more than 16 binades.
+// part: compensated FP32 summation in which every addition's rounding error
+// is recovered exactly with TwoSum and added to a separate error sum; the
+// represented value is fs + fe (error of order u^2 times sum|x| rather than
+// the 2u sum|x| of Kahan's recurrence).  FP32 payloads feed every element;
+// BF16 and FP8 payloads feed per-vector sums (exact for FP8, see
+// vec_sum_fp8; for BF16 exact unless the eight values span more than 16
+// binades).
 template <int DT>
 struct Acc {
     uint32_t s = 0, xl = 0, xh = 0;
     uint32_t n = 0;  // 16-byte loads folded by this thread (the host keeps it below 2^32)
-    float ks = 0.0f, kc = 0.0f;
+    float fs = 0.0f, fe = 0.0f;
 
-    __device__ __forceinline__ void kahan(float p) {
-        const float y = p - kc;
-        const float t = ks + y;
-        kc = (t - ks) - y;
-        ks = t;
+    __device__ __forceinline__ void add(float x) {
+        const float t = fs + x;
+        const float bp = t - fs;
+        fe += (fs - (t - bp)) + (x - bp);  // exact rounding error of fs + x (Knuth's TwoSum)
+        fs = t;
     }
 
     __device__ __forceinline__ void fold(const uint4& v) {
@@ -137,12 +138,12 @@ struct Acc {
         xl ^= v.x ^ v.z;
         xh ^= v.y ^ v.w;
         if constexpr (DT == SL_F32) {
-            kahan(__uint_as_float(v.x));
-            kahan(__uint_as_float(v.y));
-            kahan(__uint_as_float(v.z));
-            kahan(__uint_as_float(v.w));
+            add(__uint_as_float(v.x));
+            add(__uint_as_float(v.y));
+            add(__uint_as_float(v.z));
+            add(__uint_as_float(v.w));
         } else if constexpr (DT != SL_U32) {
-            kahan(vec_sum<DT>(v));
+            add(vec_sum<DT>(v));
         }
     }
 };
@@ -275,7 +276,7 @@ __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint3
     if (folds) {
         uint32_t s = acc.s;
         uint64_t x = (static_cast<uint64_t>(acc.xh) << 32) | acc.xl, n = acc.n;
-        float hi = acc.ks, lo = -acc.kc;
+        float hi = acc.fs, lo = acc.fe;
         warp_merge<DT>(s, x, n, hi, lo);
         if (lane == 0) {
             WarpPartial p;

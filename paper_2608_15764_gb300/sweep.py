@@ -210,8 +210,8 @@ PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
 
 def run_prec(out: str | None, repeats: int = 5, gib: float = 1.0, verbose: bool = True):
     """Precision form: N(0,1) payloads (float32, bfloat16, FP8-E4M3 x8) of
-    `gib` GiB through every mechanism; GB/s and the error of the FP32-Kahan /
-    FP64-combine sum against the FP64 oracle (relative, and normalised by
+    `gib` GiB through every mechanism; GB/s and the error of the compensated
+    FP32 / FP64-combine sum against the FP64 oracle (relative, and normalised by
     sum|x|), plus the uint32 checksum against the oracle."""
     import math
     from concurrent.futures import ThreadPoolExecutor
