@@ -316,19 +316,40 @@ def run_ours(a):
         return 0
 
     # ---- end to end through the public host-buffer entry point
+    # Staged: 256 MiB copies to device staging overlapped with the kernel on
+    # the previous chunk.  Direct: one kernel reads the pinned host buffer in
+    # place over the CPU-GPU link (longer latency: more bytes in flight).  The
+    # faster measured mode is reported.
     host = host_buffer(nbytes, pinned=True)
-    sl.sl_run_host(host, dtype=sl.SL_U32, cfg=cfg)  # warm (staging allocation)
-    e2e_t = []
-    for _ in range(a.e2e_steps):
-        t0 = time.perf_counter()
-        rh = sl.sl_run_host(host, dtype=sl.SL_U32, cfg=cfg)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_value = nbytes * len(e2e_t) / sum(e2e_t) / 1e9
+    e2e_cands = [("staged", best.label(), cfg)]
+    for label, pt in [("direct", "ldgdyn:16:256"), ("direct", "ldgdyn:8:512"), ("direct", "ldgdyn:12:256"),
+                      ("direct", "tma:65536:3:256"), ("direct", "tma:16384:8:512")]:
+        p = tune.parse_point(pt)
+        e2e_cands.append((label, p.label(), p.cfg(host_direct=True)))
+    e2e_all = []
+    for mode, label, c in e2e_cands:
+        try:
+            sl.sl_run_host(host, dtype=sl.SL_U32, cfg=c)  # warm (staging allocation, page mapping)
+        except sl.SLError as e:
+            e2e_all.append({"mode": mode, "point": label, "status": e.status})
+            continue
+        ts = []
+        for _ in range(a.e2e_steps):
+            t0 = time.perf_counter()
+            r_ = sl.sl_run_host(host, dtype=sl.SL_U32, cfg=c)
+            ts.append(time.perf_counter() - t0)
+        e2e_all.append({"mode": mode, "point": label, "gbs": round(nbytes * len(ts) / sum(ts) / 1e9, 2),
+                        "result": r_})
+    ok = [e for e in e2e_all if "gbs" in e]
+    e2e_best = max(ok, key=lambda e: e["gbs"])
+    e2e_value = e2e_best["gbs"]
+    rh = e2e_best["result"]
+    e2e_host_ok = all((e["result"].sum_u32, e["result"].xor_u64) == (rh.sum_u32, rh.xor_u64) for e in ok)
 
     # ---- CPU oracle on the host cores (bounded sample) and parity
     words = host.numpy().view("uint32")
     oc, cpu_gbs, threads, passes, el = cpu_oracle(words, a.cpu_seconds)
-    parity = (res[0].sum_u32, res[0].xor_u64) == oc and (rh.sum_u32, rh.xor_u64) == oc
+    parity = (res[0].sum_u32, res[0].xor_u64) == oc and (rh.sum_u32, rh.xor_u64) == oc and e2e_host_ok
 
     peak, peak_kind = _peaks()
     kern_ms = statistics.mean(step_ms)
@@ -352,7 +373,9 @@ def run_ours(a):
                          "sample": f"{passes} full passes over the {nbytes >> 20} MiB host buffer "
                                    f"({el:.1f} s wall, {threads} threads)"},
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": sl.RESULT_BYTES, "api": "sl_run_host (pinned host buffer, 256 MiB chunks)"},
+                "d2h_bytes_per_step": sl.RESULT_BYTES,
+                "api": f"sl_run_host, pinned host buffer, {e2e_best['mode']} mode, {e2e_best['point']}",
+                "modes": [{k: v for k, v in e.items() if k != "result"} for e in e2e_all]},
         "gpu_launches": a.steps,
         "clocks": clk,
         "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent)},

@@ -106,7 +106,10 @@ typedef struct sl_config {
                             consumers' bounded wait expires (failure-detection
                             test: the call returns SL_ERR_TIMEOUT and the CUDA
                             context stays usable) */
-    int32_t reserved;
+    int32_t host_direct; /* sl_run_host only: nonzero = the load kernel reads the
+                            host buffer directly over the CPU-GPU link (pinned
+                            memory, or pageable memory where the device can
+                            address it), with no staging copies */
     void*   stream;      /* cudaStream_t to launch on; NULL = legacy default stream */
 } sl_config;
 
@@ -215,10 +218,13 @@ int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config
              sl_result* out);
 
 /* End-to-end form: the payload is in HOST memory (page-locked for full
- * speed).  Copies it to a library-owned device staging ring in chunks of
- * 256 MiB on a copy stream, overlapped with the load kernel on each chunk,
- * then combines all chunks and copies the result back.  device_ns covers the
- * whole call (first copy to result on the host).  Synchronous. */
+ * speed).  Staged mode (cfg->host_direct == 0): copies it to a library-owned
+ * device staging ring in chunks of 256 MiB on a copy stream, overlapped with
+ * the load kernel on each chunk, then combines all chunks.  Direct mode
+ * (cfg->host_direct != 0): one load kernel reads the host buffer in place
+ * through its device mapping (SL_ERR_ARG if the device cannot address it).
+ * Either way the result is copied back and device_ns covers the whole call
+ * (first transfer to result on the host).  Synchronous. */
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
                 sl_result* out);
 

@@ -46,7 +46,7 @@ class sl_config(ctypes.Structure):
         ("passes", ctypes.c_int32),
         ("cop", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("host_direct", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 

@@ -485,6 +485,39 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
     if (rc) return rc;
     std::lock_guard<std::recursive_mutex> g(c->mu);
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+    if (cfg->host_direct) {
+        // The kernel reads the host buffer in place: pinned memory through its
+        // device mapping, pageable memory where the device can address it.
+        const void* dptr = nullptr;
+        if (bytes > 0) {
+            cudaPointerAttributes pa;
+            if (cudaPointerGetAttributes(&pa, host_buf) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                pa.devicePointer) {
+                dptr = pa.devicePointer;
+            } else {
+                (void)cudaGetLastError();
+                int pageable = 0;
+                cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c->dev);
+                (void)cudaGetLastError();
+                if (!pageable) return fail(SL_ERR_ARG, "the device cannot address this host buffer directly");
+                dptr = host_buf;
+            }
+        }
+        CUDA_TRY(cudaEventRecord(c->ev0, s));
+        Plan p;
+        int rc2 = enqueue_locked(c, dptr, bytes, dtype, cfg, c->dres, false, &p);
+        if (rc2) return rc2;
+        CUDA_TRY(cudaMemcpyAsync(c->hres, c->dres, sizeof(sl_result), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaEventRecord(c->ev1, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        *out = *c->hres;
+        out->device_ns = static_cast<uint64_t>(static_cast<double>(ms) * 1e6 + 0.5);
+        fill_shape(p, out);
+        if (out->status != SL_OK) return fail(out->status, "a bounded device wait timed out");
+        return SL_OK;
+    }
     if (!c->stage[0]) {
         for (int b = 0; b < 2; ++b) {
             CUDA_TRY(cudaMalloc(&c->stage[b], HOST_CHUNK));

@@ -60,6 +60,7 @@ def test_run_host_multi_chunk(sl):
     host = workloads.splitmix_u32(7, nbytes // 4)
     want = _oracle_parallel(host)
     pinned = torch.from_numpy(host.view(np.uint8)).pin_memory()
-    for cfg in [sl.config("ldg", k=2), sl.config("cpasync", k=4), sl.config("tma", stage_bytes=65536, stages=3)]:
+    for cfg in [sl.config("ldg", k=2), sl.config("cpasync", k=4), sl.config("tma", stage_bytes=65536, stages=3),
+                sl.config("ldg", k=16, order="dyn", host_direct=True)]:
         r = sl.sl_run_host(pinned, dtype=sl.SL_U32, cfg=cfg)
         assert (r.sum_u32, r.xor_u64) == want and r.issued_loads == nbytes // 16

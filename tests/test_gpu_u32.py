@@ -227,7 +227,11 @@ def test_enqueue_many_on_one_stream(sl, data):
 
 
 @pytest.mark.parametrize("mech,kw", [("ldg", {"k": 4}), ("tma", {"stage_bytes": 16384, "stages": 4}),
-                                     ("ldg", {"k": 4, "order": "dyn"})])
+                                     ("ldg", {"k": 4, "order": "dyn"}),
+                                     ("ldg", {"k": 8, "order": "dyn", "host_direct": True}),
+                                     ("ldg", {"k": 3, "host_direct": True}),
+                                     ("tma", {"stage_bytes": 65536, "stages": 3, "host_direct": True}),
+                                     ("cpasync", {"k": 4, "host_direct": True})])
 def test_run_host_matches(sl, data, mech, kw):
     _, host, want = data
     pinned = torch.from_numpy(host.view(np.uint8)).pin_memory()
