@@ -88,7 +88,7 @@ def parse_point(text: str) -> Point:
 def default_points(cta: int = 256) -> list[Point]:
     pts = [Point(SL_LDG, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8, 12, 16)]
     pts += [Point(SL_LDG, k=k, cta=cta, cop=1) for k in (1, 2, 4, 8)]
-    pts += [Point(SL_LDG, k=k, cta=cta, order=2) for k in (2, 3, 4, 6, 8)]
+    pts += [Point(SL_LDG, k=k, cta=cta, order=2) for k in (2, 3, 4, 6, 8, 12, 16)]
     pts += [Point(SL_LDG, k=k, cta=512, order=2) for k in (2, 4)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in (1, 2, 4, 8)]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n)
