@@ -67,7 +67,11 @@ extern "C" {
 
 /* ---- enums ------------------------------------------------------------ */
 typedef enum { SL_U32 = 0, SL_F32 = 1, SL_BF16 = 2, SL_FP8_E4M3 = 3 } sl_dtype;
-typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2 } sl_mech;
+/* SL_LDSTS: the matched plain-load kernel of paper §4.3 -- G independent
+ * 16-byte ld.global per thread, stored to the thread's shared-memory slots
+ * with st.shared, read back and folded (cp.async's round trip with the data
+ * passing through registers); G = k, 1..16. */
+typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2, SL_LDSTS = 3 } sl_mech;
 /* Traversal of the buffer by the CTAs.  SL_ASC / SL_DESC: CTA b takes tiles
  * b, b+grid, ... from the first (or last) tile on (the paper's layout).
  * SL_DYN (LDG only): CTAs claim contiguous chunks of about 1 MiB from an
@@ -79,7 +83,7 @@ typedef enum { SL_ASC = 0, SL_DESC = 1, SL_DYN = 2 } sl_order;
 typedef enum { SL_COP_CG = 0, SL_COP_CG_L2_256 = 1, SL_COP_NC_NA_L2_256 = 2 } sl_cop;
 
 #define SL_MAX_K 16
-#define SL_MAX_D 8
+#define SL_MAX_D 16
 #define SL_MIN_STAGES 2
 #define SL_MAX_STAGES 8
 
@@ -88,7 +92,9 @@ typedef struct sl_config {
     int32_t mech;        /* sl_mech */
     int32_t k;           /* SL_LDG: K = independent 16-byte loads per thread per
                             iteration, 1..16.  SL_CPASYNC: D = commit groups in
-                            flight per thread, 1..8.  SL_TMA: ignored. */
+                            flight per thread, 1..16.  SL_LDSTS: G = loads per
+                            thread staged through shared memory, 1..16.
+                            SL_TMA: ignored. */
     int32_t stage_bytes; /* SL_TMA: bytes per ring stage, 4096, 16384 or 65536 */
     int32_t stages;      /* SL_TMA: ring depth, 2..8 */
     int32_t cta;         /* threads per CTA that fold loads, a multiple of 32:

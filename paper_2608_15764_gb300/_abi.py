@@ -26,10 +26,10 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_ALIGN", -3: "SL_ERR_IN
 
 # enums
 SL_U32, SL_F32, SL_BF16, SL_FP8_E4M3 = 0, 1, 2, 3
-SL_LDG, SL_CPASYNC, SL_TMA = 0, 1, 2
+SL_LDG, SL_CPASYNC, SL_TMA, SL_LDSTS = 0, 1, 2, 3
 SL_ASC, SL_DESC, SL_DYN = 0, 1, 2
 SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256 = 0, 1, 2
-SL_MAX_K, SL_MAX_D, SL_MIN_STAGES, SL_MAX_STAGES = 16, 8, 2, 8
+SL_MAX_K, SL_MAX_D, SL_MIN_STAGES, SL_MAX_STAGES = 16, 16, 2, 8
 SL_DEBUG_TMA_SKIP_STAGE = 1
 
 

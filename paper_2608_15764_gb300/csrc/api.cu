@@ -241,8 +241,11 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
         p->warps = cta / 32;
         break;
     case SL_CPASYNC:
-        if (cfg->k < 1 || cfg->k > SL_MAX_D) return fail(SL_ERR_ARG, "cp.async depth %d not in 1..%d", cfg->k, SL_MAX_D);
-        p->fn = sl::cpasync_kernel(dtype, cfg->k);
+    case SL_LDSTS:
+        if (cfg->k < 1 || cfg->k > SL_MAX_D)
+            return fail(SL_ERR_ARG, "%s depth %d not in 1..%d", cfg->mech == SL_CPASYNC ? "cp.async" : "ld/st.shared",
+                        cfg->k, SL_MAX_D);
+        p->fn = cfg->mech == SL_CPASYNC ? sl::cpasync_kernel(dtype, cfg->k) : sl::ldsts_kernel(dtype, cfg->k);
         p->block = cta;
         p->smem = static_cast<size_t>(cfg->k) * cta * 16;
         tile_vec = static_cast<uint64_t>(cta) * cfg->k;
@@ -276,7 +279,7 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     // K in-flight 16-byte loads need 4K registers.  Where the CTA size caps
     // registers below that (CTA 1024 with large K), the compiler interleaves
     // loads with folds and K would no longer be the offered ILP.
-    if (cfg->mech == SL_LDG && fi->regs < 4 * cfg->k + 16)
+    if ((cfg->mech == SL_LDG || cfg->mech == SL_LDSTS) && fi->regs < 4 * cfg->k + 16)
         return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d loads in flight at cta %d",
                     fi->regs, cfg->k, cta);
     if (p->block > fi->max_threads)

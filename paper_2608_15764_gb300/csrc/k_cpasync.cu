@@ -90,6 +90,14 @@ static const void* cpasync_for(int d) {
     case 6: return reinterpret_cast<const void*>(&k_cpasync<6, DT>);
     case 7: return reinterpret_cast<const void*>(&k_cpasync<7, DT>);
     case 8: return reinterpret_cast<const void*>(&k_cpasync<8, DT>);
+    case 9: return reinterpret_cast<const void*>(&k_cpasync<9, DT>);
+    case 10: return reinterpret_cast<const void*>(&k_cpasync<10, DT>);
+    case 11: return reinterpret_cast<const void*>(&k_cpasync<11, DT>);
+    case 12: return reinterpret_cast<const void*>(&k_cpasync<12, DT>);
+    case 13: return reinterpret_cast<const void*>(&k_cpasync<13, DT>);
+    case 14: return reinterpret_cast<const void*>(&k_cpasync<14, DT>);
+    case 15: return reinterpret_cast<const void*>(&k_cpasync<15, DT>);
+    case 16: return reinterpret_cast<const void*>(&k_cpasync<16, DT>);
     default: return nullptr;
     }
 }

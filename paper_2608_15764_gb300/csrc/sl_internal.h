@@ -54,6 +54,7 @@ enum : uint32_t { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT_FULL = 1, DEV_ERR_TIMEOUT_EM
 const void* ldg_kernel(int dtype, int k, int cta, int cop);
 const void* ldg_dyn_kernel(int dtype, int k, int cta);
 const void* cpasync_kernel(int dtype, int d);
+const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
 
 // Record a failure message for sl_last_error(); returns code (api.cu).

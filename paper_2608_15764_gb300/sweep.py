@@ -19,6 +19,15 @@ GPU and checked against the first cell's checksum):
        stage {4,16,64} KiB x stages 2..8 (cells over the shared-memory limit
        are recorded as infeasible).
   c4   allocations 512 MiB, 1, 2, 4, 8, 16, 20 GiB; LDG K in {1,2,4,8,16}.
+  cpratio  paper §4.3: cp.async against the matched ld.global -> st.shared
+       kernel at equal offered groups G in {1,2,4,8,12,16} (cp.async depth D =
+       G; G loads staged through shared memory), at 1 and 8 warps per SM (one
+       CTA per SM), on 1 GiB.
+  l2   the L2-targeted backend (paper §4.2 "L2-targeted control"): 16, 32
+       and 64 MiB buffers (below the 129 MB L2) read 4 GiB / size passes per
+       launch, LDG K in {1,2,3,4,6,8,12,16} at 256 threads x 4 x SMs and
+       K in {1,2,4,8} at the primary shape; cells legitimately exceed the
+       HBM datasheet.
   ilp  one CTA of one warp (32 threads) on a 32 MiB buffer: time versus K
        (LDG) and D (cp.async).  With all K loads in flight, a lone warp is
        latency-bound and its time falls about K-fold at fixed work.
@@ -90,6 +99,18 @@ def _cells(config: str, sms: int):
     elif config == "primary":
         for k in (1, 2, 4, 8):
             yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=4)
+    elif config == "cpratio":
+        for warps in (1, 8):
+            for g in (1, 2, 4, 8, 12, 16):
+                for mech in ("cpasync", "ldsts"):
+                    yield dict(mech=mech, k=g, cta=32 * warps, grid=sms, gib=1, warps_per_sm=warps)
+    elif config == "l2":
+        for mib in (16, 32, 64):
+            passes = (4 << 30) // (mib << 20)  # 4 GiB issued at every size
+            for k in (1, 2, 3, 4, 6, 8, 12, 16):
+                yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=mib / 1024, passes=passes)
+            for k in (1, 2, 4, 8):
+                yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=mib / 1024, passes=passes)
     elif config == "ncu-points":
         from .tune import default_points
         for p in default_points():
@@ -151,7 +172,8 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
             seq = todo if order == "asc" else list(reversed(todo))
             cfgs, keep = [], []
             for c in seq:
-                kw = dict(cta=c["cta"], grid=c["grid"])
+                passes = c.get("passes", 1)
+                kw = dict(cta=c["cta"], grid=c["grid"], passes=passes)
                 if c["mech"] == "tma":
                     cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
                 else:
@@ -178,8 +200,9 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
             res = sl.sl_sweep(buf, cfgs, dtype=sl.SL_U32, repeats=repeats, warmup=warmup, sweep_order="asc")
             for row, rr in zip(keep, res):
                 ok = [r for r in rr if r.status == 0]
-                gbs = [nbytes / r.device_ns for r in ok if r.device_ns]
-                wgbs = [nbytes / r.window_ns for r in ok if r.window_ns]
+                vol = nbytes * row.get("passes", 1)  # bytes issued per launch
+                gbs = [vol / r.device_ns for r in ok if r.device_ns]
+                wgbs = [vol / r.window_ns for r in ok if r.window_ns]
                 cks = {(r.sum_u32, r.xor_u64) for r in ok}
                 if ref is None and cks:
                     ref = next(iter(cks))
@@ -191,7 +214,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                     gbs_max=round(max(gbs), 2) if gbs else None,
                     gbs=[round(v, 2) for v in gbs],
                     window_gbs_median=round(statistics.median(wgbs), 2) if wgbs else None,
-                    issued_ok=all(r.issued_loads == nbytes // 16 for r in ok),
+                    issued_ok=all(r.issued_loads == vol // 16 for r in ok),
                     checksum_ok=(cks == {ref}),
                     above_datasheet=bool(gbs and max(gbs) > DATASHEET_GBS),
                     frac_of_datasheet=round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,
@@ -275,6 +298,19 @@ def _emit(out, row, verbose):
                           "gbs": row.get("gbs_median"), "res": row.get("resident_per_sm")}), flush=True)
 
 
+def cp_ratio(rows):
+    """cp.async / matched-plain-load bandwidth ratio per (warps per SM, G,
+    order) -- the quantity of paper §4.3."""
+    by = {}
+    for r in rows:
+        if r.get("config") != "cpratio" or r.get("status") or r.get("gbs_median") is None:
+            continue
+        by.setdefault((r["warps_per_sm"], r["k"], r["order"]), {})[r["mech"]] = r["gbs_median"]
+    return [{"warps_per_sm": w, "groups": g, "order": o, "cpasync_gbs": d["cpasync"], "ldsts_gbs": d["ldsts"],
+             "ratio": round(d["cpasync"] / d["ldsts"], 3)}
+            for (w, g, o), d in sorted(by.items()) if "cpasync" in d and "ldsts" in d]
+
+
 def summarize(rows):
     """K=2 -> K=8 endpoint change per (config group, order) where both exist."""
     out = []
@@ -294,7 +330,8 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "prec"])
+                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "prec", "l2",
+                             "cpratio"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
@@ -309,6 +346,8 @@ def main(argv=None):
     rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if ncu else 1)
     for s in summarize(rows):
         print(json.dumps({"summary": s}), flush=True)
+    for s in cp_ratio(rows):
+        print(json.dumps({"cp_ratio": s}), flush=True)
     print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
 
 

@@ -77,6 +77,12 @@ def test_ldg_dynamic_float(sl, payloads, dt, k):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("g", [1, 5, 12])
+def test_ldsts_float(sl, payloads, dt, g):
+    _check(sl, payloads[dt], dt, sl.config("ldsts", k=g, cta=256))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("d", [1, 2, 4, 8])
 def test_cpasync_float(sl, payloads, dt, d):
     _check(sl, payloads[dt], dt, sl.config("cpasync", k=d, cta=256))

@@ -78,6 +78,16 @@ def test_cpasync_every_depth(sl, data, d, cta, order):
     _check(sl, dev, NBYTES, want, sl.config("cpasync", k=d, cta=cta, order=order))
 
 
+@pytest.mark.parametrize("g", list(range(1, 17)))
+@pytest.mark.parametrize("cta", [32, 256])
+def test_ldsts_and_deep_cpasync(sl, data, g, cta):
+    """The matched ld.global -> st.shared kernel (paper §4.3) at every offered
+    group count, and cp.async at the same depths (up to 16)."""
+    dev, _, want = data
+    _check(sl, dev, NBYTES, want, sl.config("ldsts", k=g, cta=cta))
+    _check(sl, dev, NBYTES, want, sl.config("cpasync", k=g, cta=cta, order="desc"))
+
+
 @pytest.mark.parametrize("stage", [4096, 16384, 65536])
 @pytest.mark.parametrize("stages", [2, 3, 4, 8])
 @pytest.mark.parametrize("order", ["asc", "desc"])

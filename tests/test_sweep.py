@@ -56,3 +56,12 @@ def test_summarize_endpoint_change():
     s = sweep.summarize(rows)
     assert s == [{"config": "c1", "gib": 1, "cta": 256, "grid": 608, "order": "asc", "k2": 3058.8,
                   "k8": 1988.7, "change_pct": -34.98}]
+
+
+def test_cp_ratio_pairs_mechanisms():
+    rows = [{"config": "cpratio", "status": 0, "warps_per_sm": 1, "k": 16, "order": "asc", "mech": m, "gbs_median": v}
+            for m, v in (("cpasync", 290.0), ("ldsts", 100.0))]
+    assert sweep.cp_ratio(rows) == [{"warps_per_sm": 1, "groups": 16, "order": "asc", "cpasync_gbs": 290.0,
+                                     "ldsts_gbs": 100.0, "ratio": 2.9}]
+    cells = list(sweep._cells("cpratio", 152))
+    assert len(cells) == 2 * 6 * 2 and {c["cta"] for c in cells} == {32, 256}
