@@ -234,6 +234,30 @@ int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
                 sl_result* out);
 
+/* ---- pointer-chase latency probe ---------------------------------------- */
+
+typedef struct sl_chase_result {
+    uint32_t final_index;    /* word index reached after warm + hops steps */
+    uint32_t reserved;
+    uint64_t hops;           /* timed steps */
+    uint64_t ns;             /* %globaltimer over the timed steps */
+    uint64_t cycles;         /* clock64 (SM cycles) over the timed steps */
+    double   ns_per_hop;
+    double   cycles_per_hop;
+} sl_chase_result;
+
+/* Unloaded load latency (paper §4.1 "Primitive baseline": a dependent pointer
+ * chain on a single SM, .ca and .cg).  dev_chain holds uint32 word indices:
+ * from word `start`, one thread replaces the index by the word it points to,
+ * first `warm` untimed steps (to bring the chain into the cache level that
+ * holds it), then `hops` timed steps; each load depends on the previous one.
+ * cache_l1 nonzero loads with ld.global.ca (L1-allocating), else .cg (L2).
+ * bytes: chain size (a multiple of 4).  SL_ERR_ARG if an index leaves the
+ * chain.  Synchronous on `stream`.  Chains come from any generator; the
+ * library's tests use one random cycle through every element. */
+int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t warm, uint64_t hops, int32_t cache_l1,
+             void* stream, sl_chase_result* out);
+
 /* ---- batched form -------------------------------------------------------- */
 
 /* One device buffer of a batch (24 bytes). */

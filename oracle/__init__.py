@@ -70,6 +70,8 @@ def _load():
             lib.oracle_elem_bytes.argtypes = [ctypes.c_int32]
             lib.oracle_decode.restype = ctypes.c_int32
             lib.oracle_decode.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
+            lib.oracle_chase.restype = ctypes.c_uint32
+            lib.oracle_chase.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64]
             lib.oracle_fsum.restype = ctypes.c_int32
             lib.oracle_fsum.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -152,3 +154,10 @@ def fsum(dtype: int, payload) -> tuple[float, float]:
     if rc != 0:
         raise ValueError(f"bad dtype {dtype}")
     return float(s.value), float(a.value)
+
+
+def chase(chain, start: int, steps: int) -> int:
+    """Final word index after following the chain `steps` times from `start`
+    (paper §4.1 pointer chase); 0xFFFFFFFF if an index leaves the buffer."""
+    w = _words(chain)
+    return int(_load().oracle_chase(w.ctypes.data, w.size, start, steps))

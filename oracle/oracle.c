@@ -23,6 +23,9 @@
  *    (iterations = floor(L / (threads*K))) and its mismatch are also given so
  *    the printed 0.024576% can be reconstructed.
  *
+ *  - Paper §4.1 "Primitive baseline": a dependent pointer chase -- follow a
+ *    chain of word indices a given number of steps (oracle_chase).
+ *
  *  - Float payloads (precision form; no paper counterpart): the exact sum of
  *    the decoded values, computed as an FP64 Neumaier (improved Kahan-Babuska)
  *    sum in element order, plus the sum of absolute values.  Decoders follow
@@ -216,4 +219,20 @@ int32_t oracle_fsum(int32_t dtype, const void *payload, uint64_t n,
     *sum_out = s + c;
     *abs_out = a;
     return 0;
+}
+
+/* ---- pointer chase ------------------------------------------------------ */
+
+/* Paper §4.1 "Primitive baseline": a dependent pointer chain.  Starting at word
+ * index `start`, replace the index by the word it points to, `steps` times, and
+ * return the final index (or 0xFFFFFFFF if an index leaves the buffer). */
+uint32_t oracle_chase(const uint32_t *chain, uint64_t nwords, uint32_t start, uint64_t steps)
+{
+    uint32_t idx = start;
+    for (uint64_t s = 0; s < steps; ++s) {
+        if ((uint64_t)idx >= nwords)
+            return 0xFFFFFFFFu;
+        idx = chain[idx];
+    }
+    return idx;
 }

@@ -21,7 +21,8 @@ from ._abi import (  # noqa: F401  (re-exported constants)
     SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_DYN, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
     SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_LDSTS, SL_MAX_D, SL_MAX_K,
     SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_TMA, SL_U32,
-    STATUS_NAMES, RESULT_BYTES, load, sl_batch_desc, sl_config, sl_devinfo, sl_result, sl_tune_entry,
+    STATUS_NAMES, RESULT_BYTES, load, sl_batch_desc, sl_chase_result, sl_config, sl_devinfo, sl_result,
+    sl_tune_entry,
 )
 
 MECHS = {"ldg": SL_LDG, "cpasync": SL_CPASYNC, "tma": SL_TMA, "ldsts": SL_LDSTS}
@@ -242,3 +243,13 @@ def sl_batch_destroy(b: sl_batch) -> None:
     if b.handle:
         load().sl_batch_destroy(b.handle)
         b.handle = None
+
+
+def sl_chase(chain, start: int = 0, warm: int = 0, hops: int = 1 << 16, cache_l1: bool = False, nbytes=None,
+             stream=None) -> sl_chase_result:
+    """Pointer-chase latency probe: one thread follows the chain (uint32 word
+    indices) `warm` untimed then `hops` timed steps from word `start`."""
+    r = sl_chase_result()
+    _check(load().sl_chase(_addr(chain), _nbytes(chain, nbytes), int(start), int(warm), int(hops),
+                           int(bool(cache_l1)), _stream_handle(stream), ctypes.byref(r)))
+    return r

@@ -99,6 +99,12 @@ class sl_devinfo(ctypes.Structure):
         return d
 
 
+class sl_chase_result(ctypes.Structure):
+    _fields_ = [("final_index", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("hops", ctypes.c_uint64),
+                ("ns", ctypes.c_uint64), ("cycles", ctypes.c_uint64), ("ns_per_hop", ctypes.c_double),
+                ("cycles_per_hop", ctypes.c_double)]
+
+
 class sl_batch_desc(ctypes.Structure):
     _fields_ = [("ptr", ctypes.c_void_p), ("bytes", ctypes.c_uint64), ("dtype", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
@@ -130,6 +136,7 @@ PROTOTYPES = {
                         ctypes.POINTER(sl_result)]),
     "sl_run_host": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), ctypes.POINTER(sl_result)]),
     "sl_run_noalloc": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), _P]),
+    "sl_chase": (_I32, [_P, _U64, ctypes.c_uint32, _U64, _U64, _I32, _P, ctypes.POINTER(sl_chase_result)]),
     "sl_batch_create": (_I32, [ctypes.POINTER(sl_batch_desc), _I32, ctypes.POINTER(sl_tune_entry), _I32,
                                ctypes.POINTER(ctypes.c_void_p)]),
     "sl_batch_run": (_I32, [_P, ctypes.POINTER(sl_result), ctypes.POINTER(ctypes.c_uint64)]),

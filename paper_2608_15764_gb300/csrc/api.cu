@@ -479,6 +479,35 @@ int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config
     return SL_OK;
 }
 
+int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t warm, uint64_t hops, int32_t cache_l1,
+             void* stream, sl_chase_result* out) {
+    if (!out || !dev_chain) return fail(SL_ERR_ARG, "NULL argument");
+    if ((bytes & 3u) || (reinterpret_cast<uintptr_t>(dev_chain) & 3u))
+        return fail(SL_ERR_ALIGN, "chain must be 4-byte aligned and a multiple of 4 bytes");
+    if (bytes / 4 == 0 || start >= bytes / 4) return fail(SL_ERR_ARG, "start index outside the chain");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t* dout = reinterpret_cast<uint64_t*>(c->dres);  // sl_result scratch holds 4 words
+    CUDA_TRY(sl::launch_chase(static_cast<const uint32_t*>(dev_chain), bytes / 4, start, warm, hops, cache_l1 ? 1 : 0,
+                              dout, s));
+    uint64_t h[4];
+    CUDA_TRY(cudaMemcpyAsync(c->hres, dout, sizeof h, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::memcpy(h, c->hres, sizeof h);
+    if (h[3]) return fail(SL_ERR_ARG, "the chain left the buffer (an index beyond its end)");
+    out->final_index = static_cast<uint32_t>(h[0]);
+    out->reserved = 0;
+    out->hops = hops;
+    out->ns = h[1];
+    out->cycles = h[2];
+    out->ns_per_hop = hops ? static_cast<double>(h[1]) / hops : 0.0;
+    out->cycles_per_hop = hops ? static_cast<double>(h[2]) / hops : 0.0;
+    return SL_OK;
+}
+
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
     if (!out || !cfg) return fail(SL_ERR_ARG, "NULL argument");
     if (bytes > 0 && !host_buf) return fail(SL_ERR_ARG, "host buffer is NULL");

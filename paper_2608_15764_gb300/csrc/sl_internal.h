@@ -57,6 +57,10 @@ const void* cpasync_kernel(int dtype, int d);
 const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
 
+// Pointer chase (k_chase.cu): out[4] = final index, ns, cycles, out-of-range flag.
+cudaError_t launch_chase(const uint32_t* chain, uint64_t nwords, uint32_t start, uint64_t warm, uint64_t hops,
+                         int ca, uint64_t* out, cudaStream_t s);
+
 // Record a failure message for sl_last_error(); returns code (api.cu).
 int set_error(int code, const char* msg);
 

@@ -172,3 +172,28 @@ int32_t wl_payload(int32_t dtype, uint64_t seed, uint64_t first, uint64_t n,
     }
     return 0;
 }
+
+/* Pointer-chase chain: n elements, one every `stride_words` uint32 words of
+ * `out` (n * stride_words words, zero elsewhere).  Element i holds the word
+ * index of its successor; the successor map is a single cycle through all n
+ * elements (Sattolo's algorithm, 1986), drawn with splitmix64(seed): for i
+ * from n-1 down to 1, swap p[i] with p[j], j uniform in [0, i).  Returns -1 if
+ * an index would not fit in 32 bits. */
+int32_t wl_chase_chain(uint64_t seed, uint64_t n, uint64_t stride_words, uint32_t *out, uint32_t *perm)
+{
+    if (n == 0 || n * stride_words > 0xFFFFFFFFull)
+        return -1;
+    memset(out, 0, (size_t)(n * stride_words) * sizeof(uint32_t));
+    for (uint64_t i = 0; i < n; ++i)
+        perm[i] = (uint32_t)i;
+    for (uint64_t i = n - 1, m = 0; i > 0; --i, ++m) {
+        uint64_t j = wl_splitmix64_at(seed, m) % i; /* uniform in [0, i) */
+        uint32_t t = perm[i];
+        perm[i] = perm[j];
+        perm[j] = t;
+    }
+    /* perm is a cyclic permutation: element i's successor is perm[i] */
+    for (uint64_t i = 0; i < n; ++i)
+        out[i * stride_words] = (uint32_t)(perm[i] * stride_words);
+    return 0;
+}

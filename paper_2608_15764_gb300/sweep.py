@@ -23,6 +23,7 @@ GPU and checked against the first cell's checksum):
        kernel at equal offered groups G in {1,2,4,8,12,16} (cp.async depth D =
        G; G loads staged through shared memory), at 1 and 8 warps per SM (one
        CTA per SM), on 1 GiB.
+  ladder  paper §4.1: pointer-chase latency versus footprint, .ca / .cg.
   l2   the L2-targeted backend (paper §4.2 "L2-targeted control"): 16, 32
        and 64 MiB buffers (below the 129 MB L2) read 4 GiB / size passes per
        launch, LDG K in {1,2,3,4,6,8,12,16} at 256 threads x 4 x SMs and
@@ -298,6 +299,77 @@ def _emit(out, row, verbose):
                           "gbs": row.get("gbs_median"), "res": row.get("resident_per_sm")}), flush=True)
 
 
+LADDER_FOOTPRINTS = [1 << e for e in range(13, 31)] + [24 << 20, 48 << 20, 96 << 20, 192 << 20]
+
+
+def run_ladder(out: str | None, verbose: bool = True):
+    """Paper §4.1 latency ladder: unloaded pointer-chase latency on one SM
+    versus footprint (8 KiB .. 1 GiB, one element per 64 bytes, one random
+    cycle through every element), .ca and .cg.  Each chase first walks
+    min(n, 65536) untimed steps, then times 32,768 steps; the final index is
+    checked against the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2608_15764_gb300 as sl
+    from . import workloads as wl
+
+    sl.load()
+    rows = []
+    for fp in sorted(LADDER_FOOTPRINTS):
+        n = fp // 64
+        host = wl.chase_chain(n, 64)
+        dev = torch.from_numpy(host.view(np.uint8)).cuda()
+        warm, hops = min(n, 1 << 16), 1 << 15
+        want = oracle.chase(host, 0, warm + hops)
+        for ca in (True, False):
+            r = sl.sl_chase(dev, warm=warm, hops=hops, cache_l1=ca)
+            row = {"config": "ladder", "footprint": fp, "cop": "ca" if ca else "cg", "ns_per_hop": round(r.ns_per_hop, 2),
+                   "cycles_per_hop": round(r.cycles_per_hop, 1), "final_ok": r.final_index == want}
+            rows.append(row)
+            if out:
+                with open(out, "a") as f:
+                    f.write(json.dumps(row) + "\n")
+            if verbose:
+                print(json.dumps(row), flush=True)
+        del dev
+    return rows
+
+
+def regime(values, frac: float = 0.95, tail: int = 3) -> str:
+    """Class of a response curve (values in ascending offered load), by the
+    paper's 95%-plateau rule with a three-cell tail (§3, §4.2 "Prevalence";
+    read as: saturating if every tail cell is within 95% of the maximum;
+    peak-decline if the maximum lies before the tail and the last cell is below
+    95% of it; rising-censored otherwise)."""
+    v = list(values)
+    if len(v) < tail + 1:
+        raise ValueError("curve too short")
+    top = max(v)
+    if all(x >= frac * top for x in v[-tail:]):
+        return "saturating"
+    if v.index(top) < len(v) - tail and v[-1] < frac * top:
+        return "peak-decline"
+    return "rising-censored"
+
+
+def regime_map(rows):
+    """Regime of every LDG K curve of the residency grid (config c2): one
+    curve per (CTA, resident CTAs per SM, order) over the K values present."""
+    curves = {}
+    for r in rows:
+        if r.get("config") != "c2" or r.get("status") or r.get("gbs_median") is None:
+            continue
+        curves.setdefault((r["cta"], r["resident_req"], r["order"]), {})[r["k"]] = r["gbs_median"]
+    out = {}
+    for key, byk in sorted(curves.items()):
+        ks = sorted(byk)
+        if len(ks) >= 4:
+            out[key] = regime([byk[k] for k in ks])
+    return out
+
+
 def cp_ratio(rows):
     """cp.async / matched-plain-load bandwidth ratio per (warps per SM, G,
     order) -- the quantity of paper §4.3."""
@@ -331,12 +403,16 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
                     choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "prec", "l2",
-                             "cpratio"])
+                             "cpratio", "ladder"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
     a = ap.parse_args(argv)
     t0 = time.time()
+    if a.config == "ladder":
+        rows = run_ladder(a.out)
+        print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
+        return 0
     if a.config == "prec":
         rows = run_prec(a.out, repeats=a.repeats)
         print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
@@ -348,6 +424,10 @@ def main(argv=None):
         print(json.dumps({"summary": s}), flush=True)
     for s in cp_ratio(rows):
         print(json.dumps({"cp_ratio": s}), flush=True)
+    if a.config == "c2":
+        rm = regime_map(rows)
+        counts = {c: sum(1 for v in rm.values() if v == c) for c in ("saturating", "peak-decline", "rising-censored")}
+        print(json.dumps({"regime_counts": counts, "curves": len(rm)}), flush=True)
     print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
 
 

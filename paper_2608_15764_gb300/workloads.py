@@ -71,6 +71,8 @@ def _load():
             lib.wl_f32_to_bf16.argtypes = [ctypes.c_void_p, u64, ctypes.c_void_p]
             lib.wl_f32_to_fp8_e4m3.restype = None
             lib.wl_f32_to_fp8_e4m3.argtypes = [ctypes.c_void_p, u64, ctypes.c_float, ctypes.c_void_p]
+            lib.wl_chase_chain.restype = ctypes.c_int32
+            lib.wl_chase_chain.argtypes = [u64, u64, u64, ctypes.c_void_p, ctypes.c_void_p]
             lib.wl_payload.restype = ctypes.c_int32
             lib.wl_payload.argtypes = [ctypes.c_int32, u64, u64, u64, ctypes.c_float, ctypes.c_void_p]
             _lib = lib
@@ -205,3 +207,15 @@ def batch_sizes(n: int = 1024, total: int = 16 << 30, lo: int = 64 << 10, hi: in
         rem += take
     assert sum(sizes) == total and all(lo <= v <= hi and v % 16 == 0 for v in sizes)
     return sizes
+
+
+def chase_chain(n: int, stride_bytes: int = 64, seed: int = 6) -> np.ndarray:
+    """Pointer-chase chain of n elements, one every stride_bytes (a multiple
+    of 4): word i*stride/4 holds the word index of the next element, and the
+    successor map is one random cycle through all n elements (Sattolo)."""
+    sw = stride_bytes // 4
+    out = np.empty(n * sw, dtype=np.uint32)
+    perm = np.empty(n, dtype=np.uint32)
+    if _load().wl_chase_chain(seed, n, sw, out.ctypes.data, perm.ctypes.data) != 0:
+        raise ValueError("chain too large for 32-bit word indices")
+    return out

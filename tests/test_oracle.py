@@ -219,3 +219,26 @@ def test_fsum_cancellation_is_compensated():
 def test_bad_dtype_rejected():
     with pytest.raises(ValueError):
         oracle.fsum(7, np.zeros(16, np.uint8))
+
+
+# ---- pointer chase ----------------------------------------------------------
+
+def test_chase_brute_force_and_closed_form():
+    rng = np.random.default_rng(5)
+    n, sw = 257, 3
+    succ = rng.permutation(n)
+    chain = np.zeros(n * sw, dtype=np.uint32)
+    chain[np.arange(n) * sw] = succ * sw
+    for steps in (0, 1, 2, 100, 1000):
+        idx = 0
+        for _ in range(steps):
+            idx = int(chain[idx])
+        assert oracle.chase(chain, 0, steps) == idx
+    # successor i -> i+1 (mod n): after s steps from element a, element (a+s) mod n
+    ring = np.zeros(n * sw, dtype=np.uint32)
+    ring[np.arange(n) * sw] = ((np.arange(n) + 1) % n) * sw
+    for a, s in [(0, 5), (17, 300), (256, 1)]:
+        assert oracle.chase(ring, a * sw, s) == ((a + s) % n) * sw
+    # an index outside the buffer is reported, not followed
+    bad = np.array([5, 0], dtype=np.uint32)
+    assert oracle.chase(bad, 0, 2) == 0xFFFFFFFF

@@ -65,3 +65,21 @@ def test_cp_ratio_pairs_mechanisms():
                                      "ldsts_gbs": 100.0, "ratio": 2.9}]
     cells = list(sweep._cells("cpratio", 152))
     assert len(cells) == 2 * 6 * 2 and {c["cta"] for c in cells} == {32, 256}
+
+
+def test_regime_rule():
+    assert sweep.regime([1, 2, 3, 10, 9.9, 9.8]) == "saturating"
+    assert sweep.regime([1, 10, 9, 8, 7, 6]) == "peak-decline"
+    assert sweep.regime([1, 2, 3, 4, 5, 6]) == "rising-censored"
+    # the paper's H100 primary cell (K=2 peak, -35% at K=8) is a peak-decline
+    assert sweep.regime([2000, 3059, 2700, 2300, 2100, 1989]) == "peak-decline"
+    # a maximum inside the tail that the last cell falls from is not a decline yet
+    assert sweep.regime([1, 2, 3, 10, 5, 9]) == "rising-censored"
+    with pytest.raises(ValueError):
+        sweep.regime([1, 2, 3])
+
+
+def test_regime_map_groups_curves():
+    rows = [{"config": "c2", "status": 0, "cta": 256, "resident_req": 4, "order": "asc", "k": k, "gbs_median": v}
+            for k, v in zip((1, 2, 3, 4, 6, 8), (10, 20, 30, 40, 39.5, 39))]
+    assert sweep.regime_map(rows) == {(256, 4, "asc"): "saturating"}

@@ -96,3 +96,20 @@ def test_batch_sizes_recipe():
     logs = sorted(math.log2(v) for v in s)
     assert logs[0] == 16.0 and logs[-1] <= 28.0
     assert logs[len(logs) // 2] > 20 and logs[len(logs) // 10] < logs[9 * len(logs) // 10] - 4
+
+
+@pytest.mark.parametrize("n,stride", [(2, 64), (3, 16), (1000, 64), (4096, 128)])
+def test_chase_chain_is_one_cycle(n, stride):
+    c = wl.chase_chain(n, stride)
+    sw = stride // 4
+    assert c.size == n * sw
+    mask = np.ones(c.size, bool)
+    mask[::sw] = False
+    assert not c[mask].any()                     # only element slots are used
+    seen, idx = set(), 0
+    for _ in range(n):
+        assert idx % sw == 0 and idx not in seen
+        seen.add(idx)
+        idx = int(c[idx])
+    assert idx == 0 and len(seen) == n           # a single cycle through every element
+    assert np.array_equal(c, wl.chase_chain(n, stride))
