@@ -47,17 +47,13 @@ __global__ void __launch_bounds__(G <= 8 ? 1024 : 256, 1) k_ldsts(const KArgs a)
             for (int g = 0; g < G; ++g) acc.fold(lds16(my0 + g * stride));
             ++full_iters;
         } else {
+            // ragged last tile: one vector at a time (keeps register pressure
+            // of this rare path below the main path's)
             const uint64_t rem = a.nvec - base;
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (threadIdx.x + static_cast<uint64_t>(g) * cta < rem) v[g] = ldg16<SL_COP_CG>(p + static_cast<size_t>(g) * cta);
-                else v[g] = make_uint4(0u, 0u, 0u, 0u);
-            }
-#pragma unroll
-            for (int g = 0; g < G; ++g) sts16(my0 + g * stride, v[g]);
-#pragma unroll
+#pragma unroll 1
             for (int g = 0; g < G; ++g) {
                 if (threadIdx.x + static_cast<uint64_t>(g) * cta < rem) {
+                    sts16(my0 + g * stride, ldg16<SL_COP_CG>(p + static_cast<size_t>(g) * cta));
                     acc.fold(lds16(my0 + g * stride));
                     acc.n += 1;
                 }

@@ -305,9 +305,11 @@ LADDER_FOOTPRINTS = [1 << e for e in range(13, 31)] + [24 << 20, 48 << 20, 96 <<
 def run_ladder(out: str | None, verbose: bool = True):
     """Paper §4.1 latency ladder: unloaded pointer-chase latency on one SM
     versus footprint (8 KiB .. 1 GiB, one element per 64 bytes, one random
-    cycle through every element), .ca and .cg.  Each chase first walks
-    min(n, 65536) untimed steps, then times 32,768 steps; the final index is
-    checked against the oracle."""
+    cycle through every element), .ca and .cg.  Before each chase the L2 is
+    flushed; chains of up to 4 Mi elements (256 MiB) are first walked once in
+    full (untimed), so the timed steps revisit lines that the footprint lets
+    the caches keep; longer chains are not warmed.  32,768 steps are timed and
+    the final index is checked against the oracle."""
     import numpy as np
     import torch
 
@@ -321,9 +323,11 @@ def run_ladder(out: str | None, verbose: bool = True):
         n = fp // 64
         host = wl.chase_chain(n, 64)
         dev = torch.from_numpy(host.view(np.uint8)).cuda()
-        warm, hops = min(n, 1 << 16), 1 << 15
+        warm, hops = (n if n <= (1 << 22) else 0), 1 << 15
         want = oracle.chase(host, 0, warm + hops)
         for ca in (True, False):
+            sl.sl_flush_l2()
+            torch.cuda.synchronize()
             r = sl.sl_chase(dev, warm=warm, hops=hops, cache_l1=ca)
             row = {"config": "ladder", "footprint": fp, "cop": "ca" if ca else "cg", "ns_per_hop": round(r.ns_per_hop, 2),
                    "cycles_per_hop": round(r.cycles_per_hop, 1), "final_ok": r.final_index == want}

@@ -184,7 +184,8 @@ def test_argument_errors(sl, data):
         (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", k=17)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", cta=100)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", cta=64)), sl.SL_ERR_ARG),
-        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=9)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=17)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldsts", k=0)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stage_bytes=8192)), sl.SL_ERR_INFEASIBLE),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stages=1)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stage_bytes=65536, stages=4)), sl.SL_ERR_INFEASIBLE),
