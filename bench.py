@@ -52,8 +52,10 @@ def _args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=1.5,
                     help="wall-clock seconds of the CPU-oracle sample (all cores)")
     ap.add_argument("--out", default=None, help="also append the JSON line (and curves) to this file")
-    ap.add_argument("--workload", choices=["stream", "batch"], default="stream",
-                    help="stream: the 4 GiB K-response workload (default); batch: the 1,024-buffer batched form")
+    ap.add_argument("--workload", choices=["stream", "batch", "prec"], default="stream",
+                    help="stream: the 4 GiB K-response workload (default); batch: the 1,024-buffer batched form; "
+                         "prec: the precision form (float payloads through every mechanism)")
+    ap.add_argument("--prec-gib", type=float, default=1.0, help="prec workload payload size per dtype")
     ap.add_argument("--dtypes", default="f32,bf16,fp8", help="batch workload payload dtypes")
     ap.add_argument("--batch-gib", type=float, default=16.0, help="batch workload total per dtype")
     ap.add_argument("--choice", default=None,
@@ -421,7 +423,7 @@ def run_batch(a):
     total = sum(sizes)
     offs = np.cumsum([0] + sizes[:-1])
     names = {"f32": wl.F32, "bf16": wl.BF16, "fp8": wl.FP8_E4M3, "u32": wl.U32}
-    per = []
+    per, cpu_gbs = [], []
     threads = os.cpu_count() or 1
     host = torch.empty(total, dtype=torch.uint8, pin_memory=True)
     hv = host.numpy()
@@ -463,9 +465,12 @@ def run_batch(a):
         raw = out.cpu().numpy().tobytes()
         plain = [sl.sl_result.from_buffer_copy(raw[i * sl.RESULT_BYTES:(i + 1) * sl.RESULT_BYTES])
                  for i in range(len(sizes))]
-        # parity
+        # cpu_baseline leg: the oracle's checksum of every buffer on all host
+        # cores, timed; its results are also the parity reference
+        t0 = time.perf_counter()
         with ThreadPoolExecutor(threads) as ex:
             cks = list(ex.map(lambda i: oracle.checksum(hv[offs[i]:offs[i] + sizes[i]]), range(len(sizes))))
+        cpu_gbs.append(total / (time.perf_counter() - t0) / 1e9)
         ck_ok = all((r.sum_u32, r.xor_u64, r.issued_loads) == (*ck, nb // 16) for r, ck, nb in zip(res, cks, sizes))
         ck_ok = ck_ok and all((r.sum_u32, r.xor_u64) == ck for r, ck in zip(plain, cks))
         worst = None
@@ -497,9 +502,98 @@ def run_batch(a):
             "config": {"workload": f"1,024 buffers, log-uniform 64 KiB-256 MiB, {a.batch_gib:g} GiB per dtype "
                                    "(N(0,1), FP8 x8), one device arena",
                        "l2": "inputs larger than L2; each buffer read once per launch"},
+            "cpu_baseline": {"value": round(len(cpu_gbs) / sum(1.0 / v for v in cpu_gbs), 2), "unit": "GB/s",
+                             "cores": threads, "kind": "oracle",
+                             "sample": "the oracle's uint32 checksum of all 1,024 buffers per dtype, "
+                                       "buffers spread over the host threads"},
             "per_dtype": per,
             "parity": all(p["checksums_match_oracle"] for p in per) and
             all(p["fsum_max_gated_err_sample48"] is None or p["fsum_max_gated_err_sample48"] <= 2e-6 for p in per)}
+    print(json.dumps(line), flush=True)
+    if a.out:
+        with open(a.out, "a") as f:
+            f.write(json.dumps(line) + "\n")
+    return 0 if line["parity"] else 3
+
+
+PREC_METRIC = "attained GB/s of the compensated FP32 sum (FP64 final combine) per payload dtype and mechanism"
+PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
+              [dict(mech="ldg", k=k, cta=256, order="dyn") for k in (2, 4, 8)] +
+              [dict(mech="cpasync", k=d, cta=256) for d in (2, 4, 6)] +
+              [dict(mech="tma", stage_bytes=sb, stages=n, cta=256) for sb, n in ((16384, 2), (16384, 4), (65536, 2))])
+
+
+def run_prec(a):
+    """Precision form: N(0,1) payloads of --prec-gib GiB (float32, bfloat16,
+    FP8-E4M3 x8; inputs larger than L2) through every point of PREC_CELLS,
+    `steps` timed launches each.  cpu_baseline leg: the oracle's FP64
+    Neumaier sum of the same payload on all host cores (one contiguous range
+    per thread, range sums added with math.fsum), timed; it is also the
+    reference for the error of every GPU sum, reported relative to |sum| and
+    normalised by sum|x|.  value = the harmonic mean over dtypes of each
+    dtype's fastest point."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2608_15764_gb300 as sl
+    from paper_2608_15764_gb300 import workloads as wl
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    sl.load()
+    nbytes = int(a.prec_gib * (1 << 30)) // 16 * 16
+    threads = os.cpu_count() or 1
+    per, cpu = [], []
+    worst_all = 0.0
+    clocks = ClockSampler(local)
+    for dt in (wl.F32, wl.BF16, wl.FP8_E4M3):
+        name = {wl.F32: "f32", wl.BF16: "bf16", wl.FP8_E4M3: "fp8"}[dt]
+        n = nbytes // wl.ELEM_BYTES[dt]
+        host = wl.payload(dt, n)
+        hb = host.view(np.uint8)
+        cut = [i * (n // threads) // 16 * 16 for i in range(threads)] + [n]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda i: oracle.fsum(dt, host[cut[i]:cut[i + 1]]), range(threads)))
+        cpu_s = time.perf_counter() - t0
+        cpu.append(nbytes / cpu_s / 1e9)
+        ref = math.fsum(p[0] for p in parts)
+        absum = math.fsum(p[1] for p in parts)
+        dev = torch.from_numpy(hb).cuda()
+        cfgs = [sl.config(c["mech"], **{k: v for k, v in c.items() if k != "mech"}) for c in PREC_CELLS]
+        clocks.start()
+        res = sl.sl_sweep(dev, cfgs, dtype=dt, repeats=a.steps, warmup=a.warmup)
+        clk = clocks.stop()
+        points = []
+        for c, rr in zip(PREC_CELLS, res):
+            gbs = [nbytes / r.device_ns for r in rr if r.status == 0 and r.device_ns]
+            fs = [r.fsum for r in rr]
+            err = max(abs(f - ref) for f in fs)
+            small = abs(ref) < 1e-3 * absum / max(n, 1) ** 0.5
+            gated = err / (absum if small else abs(ref))
+            worst_all = max(worst_all, gated)
+            points.append({**c, "gbs_median": round(statistics.median(gbs), 1) if gbs else None,
+                           "rel_err": err / abs(ref), "err_over_abs_sum": err / absum, "gated_err": gated,
+                           "deterministic": len(set(fs)) == 1})
+        best = max(points, key=lambda p: p["gbs_median"] or 0)
+        per.append({"dtype": name, "bytes": nbytes, "ref_fsum": ref, "abs_sum": absum, "best": best,
+                    "points": points, "clocks": clk, "oracle_gbs": round(cpu[-1], 2)})
+        del dev
+        torch.cuda.empty_cache()
+    value = len(per) / sum(1.0 / p["best"]["gbs_median"] for p in per)
+    line = {"metric": PREC_METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
+            "warmup": a.warmup, "higher_is_better": True, "data": "synthetic", "dtype": "f32,bf16,fp8",
+            "config": {"workload": f"{a.prec_gib:g} GiB N(0,1) payload per dtype (FP8 x8), one launch per step",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": round(len(cpu) / sum(1.0 / v for v in cpu), 2), "unit": "GB/s",
+                             "cores": threads, "kind": "oracle",
+                             "sample": "one FP64 Neumaier pass over each full payload, split over the host threads"},
+            "per_dtype": per, "max_gated_err": worst_all, "parity": worst_all <= 2e-6}
     print(json.dumps(line), flush=True)
     if a.out:
         with open(a.out, "a") as f:
@@ -513,6 +607,8 @@ def main(argv=None):
         return run_reference(a)
     if a.workload == "batch":
         return run_batch(a)
+    if a.workload == "prec":
+        return run_prec(a)
     return run_ours(a)
 
 

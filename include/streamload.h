@@ -71,7 +71,11 @@ typedef enum { SL_U32 = 0, SL_F32 = 1, SL_BF16 = 2, SL_FP8_E4M3 = 3 } sl_dtype;
  * 16-byte ld.global per thread, stored to the thread's shared-memory slots
  * with st.shared, read back and folded (cp.async's round trip with the data
  * passing through registers); G = k, 1..16. */
-typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2, SL_LDSTS = 3 } sl_mech;
+/* SL_LDG4: paper §4.1's streaming-read qualification row -- K independent
+ * 4-byte ld.global.cg per thread per iteration (the paper's gate is K = 1);
+ * uint32 payloads, K in {1,2,4,8,16}, cta 128/256/512/1024, SL_COP_CG, no
+ * SL_DYN.  Its issued_loads counts 4-byte loads: passes*bytes/4. */
+typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2, SL_LDSTS = 3, SL_LDG4 = 4 } sl_mech;
 /* Traversal of the buffer by the CTAs.  SL_ASC / SL_DESC: CTA b takes tiles
  * b, b+grid, ... from the first (or last) tile on (the paper's layout).
  * SL_DYN (LDG only): CTAs claim contiguous chunks of about 1 MiB from an
@@ -124,7 +128,8 @@ typedef struct sl_config {
 /* ---- results ----------------------------------------------------------- */
 typedef struct sl_result {
     uint64_t xor_u64;         /* XOR of the little-endian uint64 words read */
-    uint64_t issued_loads;    /* 16-byte logical loads folded; = passes*bytes/16 */
+    uint64_t issued_loads;    /* 16-byte logical loads folded; = passes*bytes/16
+                                 (SL_LDG4: 4-byte loads, passes*bytes/4) */
     uint64_t device_ns;       /* CUDA-event time of the load kernel (sl_run);
                                  of the whole call (sl_run_host); 0 (sl_enqueue) */
     uint64_t window_ns;       /* %globaltimer: first CTA start to last CTA end */
@@ -257,6 +262,40 @@ typedef struct sl_chase_result {
  * library's tests use one random cycle through every element. */
 int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t warm, uint64_t hops, int32_t cache_l1,
              void* stream, sl_chase_result* out);
+
+/* ---- two co-resident streams in one CTA ---------------------------------- */
+
+typedef struct sl_twostream_result {
+    uint64_t xor_u64[2];       /* [0] stream A, [1] stream B: as sl_result */
+    uint64_t issued_loads[2];  /* 16-byte loads folded: passes*bytes/16 */
+    uint64_t window_ns[2];     /* %globaltimer, earliest warp start to latest
+                                  warp end of the stream, over all CTAs */
+    uint64_t b_first_end_ns;   /* earliest end of a stream-B warp, measured
+                                  from stream A's earliest start (0: no B) */
+    uint64_t device_ns;        /* CUDA-event time of the load kernel */
+    uint32_t sum_u32[2];
+    int32_t  grid;             /* CTAs (one per SM) */
+    int32_t  cta;              /* threads per CTA = 32*(warps_a + warps_b) */
+    int32_t  b_covers_a;       /* 1 if every stream-B warp was still loading when
+                                  stream A's last warp finished (or warps_b == 0) */
+    int32_t  reserved;
+} sl_twostream_result;
+
+/* Two plain-load streams in the same CTA (paper §4.4): one CTA per SM with
+ * warps_a warps reading buf_a (bytes_a, one pass) and, after them, warps_b
+ * warps reading buf_b (bytes_b, passes_b passes), both with the LDG loop at
+ * K independent 16-byte ld.global.cg per thread (K in {1,2,4,8}).  Stream A's
+ * bandwidth is bytes_a / window_ns[0]; compared with the same call at
+ * warps_b = 0 it gives A's displacement by B.  Size B's work (passes_b) so
+ * that b_covers_a is 1, or the B load ended before A did.
+ * Arguments: warps_a >= 1, warps_b >= 0, warps_a + warps_b <= 32; buffers
+ * 16-byte aligned, bytes multiples of 16, bytes_a > 0, bytes_b > 0 when
+ * warps_b > 0 (SL_ERR_ARG / SL_ERR_ALIGN otherwise).  flush_l2 nonzero
+ * overwrites an L2-sized scratch buffer first (untimed).  Synchronous on
+ * `stream`.  The buffers stay caller-owned; the library's scratch is reused. */
+int sl_twostream(const void* buf_a, uint64_t bytes_a, const void* buf_b, uint64_t bytes_b, int32_t passes_b,
+                 int32_t warps_a, int32_t warps_b, int32_t k, int32_t flush_l2, void* stream,
+                 sl_twostream_result* out);
 
 /* ---- batched form -------------------------------------------------------- */
 

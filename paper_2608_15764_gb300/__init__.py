@@ -19,13 +19,13 @@ import ctypes
 from ._abi import (  # noqa: F401  (re-exported constants)
     SL_ASC, SL_BF16, SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256, SL_CPASYNC,
     SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_DYN, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
-    SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_LDSTS, SL_MAX_D, SL_MAX_K,
+    SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_LDG4, SL_LDSTS, SL_MAX_D, SL_MAX_K,
     SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_TMA, SL_U32,
     STATUS_NAMES, RESULT_BYTES, load, sl_batch_desc, sl_chase_result, sl_config, sl_devinfo, sl_result,
-    sl_tune_entry,
+    sl_tune_entry, sl_twostream_result,
 )
 
-MECHS = {"ldg": SL_LDG, "cpasync": SL_CPASYNC, "tma": SL_TMA, "ldsts": SL_LDSTS}
+MECHS = {"ldg": SL_LDG, "cpasync": SL_CPASYNC, "tma": SL_TMA, "ldsts": SL_LDSTS, "ldg4": SL_LDG4}
 DTYPES = {"u32": SL_U32, "f32": SL_F32, "bf16": SL_BF16, "fp8": SL_FP8_E4M3}
 ORDERS = {"asc": SL_ASC, "desc": SL_DESC, "dyn": SL_DYN}
 
@@ -243,6 +243,18 @@ def sl_batch_destroy(b: sl_batch) -> None:
     if b.handle:
         load().sl_batch_destroy(b.handle)
         b.handle = None
+
+
+def sl_twostream(buf_a, buf_b=None, warps_a: int = 1, warps_b: int = 0, k: int = 2, passes_b: int = 1,
+                 flush_l2: bool = True, nbytes_a=None, nbytes_b=None, stream=None) -> sl_twostream_result:
+    """Two plain-load streams in one CTA per SM: warps_a warps read buf_a
+    once, warps_b warps read buf_b passes_b times (paper §4.4)."""
+    r = sl_twostream_result()
+    has_b = buf_b is not None
+    _check(load().sl_twostream(_addr(buf_a), _nbytes(buf_a, nbytes_a), _addr(buf_b) if has_b else None,
+                               _nbytes(buf_b, nbytes_b) if has_b else 0, int(passes_b), int(warps_a), int(warps_b),
+                               int(k), int(bool(flush_l2)), _stream_handle(stream), ctypes.byref(r)))
+    return r
 
 
 def sl_chase(chain, start: int = 0, warm: int = 0, hops: int = 1 << 16, cache_l1: bool = False, nbytes=None,

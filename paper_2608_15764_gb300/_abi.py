@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_ALIGN", -3: "SL_ERR_IN
 
 # enums
 SL_U32, SL_F32, SL_BF16, SL_FP8_E4M3 = 0, 1, 2, 3
-SL_LDG, SL_CPASYNC, SL_TMA, SL_LDSTS = 0, 1, 2, 3
+SL_LDG, SL_CPASYNC, SL_TMA, SL_LDSTS, SL_LDG4 = 0, 1, 2, 3, 4
 SL_ASC, SL_DESC, SL_DYN = 0, 1, 2
 SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256 = 0, 1, 2
 SL_MAX_K, SL_MAX_D, SL_MIN_STAGES, SL_MAX_STAGES = 16, 16, 2, 8
@@ -105,6 +105,13 @@ class sl_chase_result(ctypes.Structure):
                 ("cycles_per_hop", ctypes.c_double)]
 
 
+class sl_twostream_result(ctypes.Structure):
+    _fields_ = [("xor_u64", ctypes.c_uint64 * 2), ("issued_loads", ctypes.c_uint64 * 2),
+                ("window_ns", ctypes.c_uint64 * 2), ("b_first_end_ns", ctypes.c_uint64),
+                ("device_ns", ctypes.c_uint64), ("sum_u32", ctypes.c_uint32 * 2), ("grid", ctypes.c_int32),
+                ("cta", ctypes.c_int32), ("b_covers_a", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class sl_batch_desc(ctypes.Structure):
     _fields_ = [("ptr", ctypes.c_void_p), ("bytes", ctypes.c_uint64), ("dtype", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
@@ -137,6 +144,8 @@ PROTOTYPES = {
     "sl_run_host": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), ctypes.POINTER(sl_result)]),
     "sl_run_noalloc": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), _P]),
     "sl_chase": (_I32, [_P, _U64, ctypes.c_uint32, _U64, _U64, _I32, _P, ctypes.POINTER(sl_chase_result)]),
+    "sl_twostream": (_I32, [_P, _U64, _P, _U64, _I32, _I32, _I32, _I32, _I32, _P,
+                            ctypes.POINTER(sl_twostream_result)]),
     "sl_batch_create": (_I32, [ctypes.POINTER(sl_batch_desc), _I32, ctypes.POINTER(sl_tune_entry), _I32,
                                ctypes.POINTER(ctypes.c_void_p)]),
     "sl_batch_run": (_I32, [_P, ctypes.POINTER(sl_result), ctypes.POINTER(ctypes.c_uint64)]),

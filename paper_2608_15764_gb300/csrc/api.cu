@@ -76,6 +76,8 @@ struct DevCtx {
     uint32_t* err = nullptr;    // control block (sl::CTRL_BYTES): error word, CTA counter, window
     sl_result* dres = nullptr;  // device result of sl_run / sl_run_host
     sl_result* hres = nullptr;  // pinned host copy
+    uint64_t* two_dev = nullptr;   // sl_twostream: timer words [0, 8) and results [8, 24)
+    uint64_t* two_host = nullptr;  // pinned copy of the results
     void* flush = nullptr;
     uint64_t flush_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -240,6 +242,18 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
         if (dyn) tile_vec *= std::max<uint64_t>(1, DYN_CHUNK_VEC / tile_vec);  // chunk of ~1 MiB
         p->warps = cta / 32;
         break;
+    case SL_LDG4:
+        if (dtype != SL_U32) return fail(SL_ERR_ARG, "SL_LDG4 reads uint32 payloads only");
+        if (cfg->cop != SL_COP_CG) return fail(SL_ERR_ARG, "SL_LDG4 has the SL_COP_CG flavour only");
+        p->fn = sl::ldg4_kernel(dtype, cfg->k, cta);
+        if (!p->fn)
+            return fail(SL_ERR_ARG, "no 4-byte LDG kernel for K %d, cta %d (K in {1,2,4,8,16}, cta 128/256/512/1024)",
+                        cfg->k, cta);
+        p->block = cta;
+        p->smem = 0;
+        tile_vec = static_cast<uint64_t>(cta) * cfg->k;  // in 4-byte words
+        p->warps = cta / 32;
+        break;
     case SL_CPASYNC:
     case SL_LDSTS:
         if (cfg->k < 1 || cfg->k > SL_MAX_D)
@@ -282,6 +296,9 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if ((cfg->mech == SL_LDG || cfg->mech == SL_LDSTS) && fi->regs < 4 * cfg->k + 16)
         return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d loads in flight at cta %d",
                     fi->regs, cfg->k, cta);
+    if (cfg->mech == SL_LDG4 && fi->regs < cfg->k + 16)
+        return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d 4-byte loads in flight at cta %d",
+                    fi->regs, cfg->k, cta);
     if (p->block > fi->max_threads)
         return fail(SL_ERR_INFEASIBLE, "%d threads per CTA exceed this kernel's limit of %d", p->block,
                     fi->max_threads);
@@ -289,7 +306,7 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (rc) return rc;
     if (p->resident < 1) return fail(SL_ERR_INFEASIBLE, "configuration has zero occupancy");
 
-    const uint64_t nvec = bytes / 16;
+    const uint64_t nvec = bytes / (cfg->mech == SL_LDG4 ? 4 : 16);  // load units: 16-byte vectors or words
     const uint64_t ntiles = (nvec + tile_vec - 1) / tile_vec;
     int64_t grid = cfg->grid;
     if (grid <= 0) grid = static_cast<int64_t>(std::min(4, p->resident)) * c->info.sm_count;
@@ -508,6 +525,95 @@ int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t war
     return SL_OK;
 }
 
+int sl_twostream(const void* buf_a, uint64_t bytes_a, const void* buf_b, uint64_t bytes_b, int32_t passes_b,
+                 int32_t warps_a, int32_t warps_b, int32_t k, int32_t flush_l2, void* stream,
+                 sl_twostream_result* out) {
+    if (!out) return fail(SL_ERR_ARG, "out is NULL");
+    if (warps_a < 1 || warps_b < 0 || warps_a + warps_b > 32)
+        return fail(SL_ERR_ARG, "warps_a %d / warps_b %d: need warps_a >= 1, warps_b >= 0, sum <= 32", warps_a, warps_b);
+    if (!sl::two_kernel(k)) return fail(SL_ERR_ARG, "K %d not in {1,2,4,8}", k);
+    if (passes_b < 0) return fail(SL_ERR_ARG, "passes_b %d < 0", passes_b);
+    if (!buf_a || bytes_a == 0) return fail(SL_ERR_ARG, "stream A needs a non-empty buffer");
+    if (warps_b > 0 && (!buf_b || bytes_b == 0)) return fail(SL_ERR_ARG, "stream B needs a non-empty buffer");
+    if ((bytes_a & 15u) || (bytes_b & 15u) || (reinterpret_cast<uintptr_t>(buf_a) & 15u) ||
+        (reinterpret_cast<uintptr_t>(buf_b) & 15u))
+        return fail(SL_ERR_ALIGN, "buffers must be 16-byte aligned and multiples of 16 bytes");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint32_t grid = static_cast<uint32_t>(c->info.sm_count);
+    const int block = 32 * (warps_a + warps_b);
+    FuncInfo* fi = nullptr;
+    rc = func_info(c, sl::two_kernel(k), 0, &fi);
+    if (rc) return rc;
+    if (fi->local_bytes > 0)
+        return fail(SL_ERR_INFEASIBLE, "this kernel spills registers (%zu bytes of local memory per thread)",
+                    fi->local_bytes);
+    if (fi->regs < 4 * k + 16)
+        return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d loads in flight", fi->regs, k);
+    int resident = 0;
+    rc = occupancy(c, sl::two_kernel(k), block, 0, &resident);
+    if (rc) return rc;
+    if (resident < 1) return fail(SL_ERR_INFEASIBLE, "a CTA of %d threads does not fit on an SM", block);
+    if (!c->two_dev) {
+        CUDA_TRY(cudaMalloc(&c->two_dev, 24 * sizeof(uint64_t)));
+        CUDA_TRY(cudaMallocHost(&c->two_host, 24 * sizeof(uint64_t)));
+    }
+    rc = ensure_scratch(c, static_cast<uint64_t>(grid) * 32);
+    if (rc) return rc;
+    sl::TwoArgs t{};
+    t.buf_a = static_cast<const uint4*>(buf_a);
+    t.buf_b = static_cast<const uint4*>(warps_b > 0 ? buf_b : buf_a);
+    t.warps_a = static_cast<uint32_t>(warps_a);
+    t.warps_b = static_cast<uint32_t>(warps_b);
+    const uint64_t pb = passes_b == 0 ? 1 : static_cast<uint64_t>(passes_b);
+    const uint64_t tv_a = 32ull * warps_a * k, tv_b = 32ull * (warps_b > 0 ? warps_b : 1) * k;
+    t.nvec_a = bytes_a / 16;
+    t.nvec_b = warps_b > 0 ? bytes_b / 16 : 0;
+    const uint64_t nt_a = (t.nvec_a + tv_a - 1) / tv_a, nt_b = (t.nvec_b + tv_b - 1) / tv_b;
+    // 32-bit tile and per-thread load counters in the kernel
+    if (nt_a + grid >= (1ull << 32) || nt_b * pb + grid >= (1ull << 32) ||
+        (nt_b * pb / grid + 1) * k >= (1ull << 32))
+        return fail(SL_ERR_ARG, "buffers or passes too large for one launch");
+    t.ntiles_a = static_cast<uint32_t>(nt_a);
+    t.total_a = static_cast<uint32_t>(nt_a);
+    t.ntiles_b = static_cast<uint32_t>(nt_b);
+    t.total_b = static_cast<uint32_t>(nt_b * pb);
+    t.parts = c->parts;
+    t.ctl = c->two_dev;
+    if (flush_l2) CUDA_TRY(sl::launch_flush(c->flush, c->flush_bytes / 16, c->info.sm_count, s));
+    // timer words: starts ~0, ends 0, B's first end ~0
+    CUDA_TRY(cudaMemsetAsync(c->two_dev + sl::TWO_START, 0xFF, 2 * sizeof(uint64_t), s));
+    CUDA_TRY(cudaMemsetAsync(c->two_dev + sl::TWO_END, 0, 2 * sizeof(uint64_t), s));
+    CUDA_TRY(cudaMemsetAsync(c->two_dev + sl::TWO_FIRST_END_B, 0xFF, sizeof(uint64_t), s));
+    CUDA_TRY(cudaEventRecord(c->ev0, s));
+    CUDA_TRY(sl::launch_two(t, k, grid, s));
+    CUDA_TRY(cudaEventRecord(c->ev1, s));
+    CUDA_TRY(sl::launch_two_combine(t, grid, c->two_dev + 8, s));
+    CUDA_TRY(cudaMemcpyAsync(c->two_host, c->two_dev + 8, 11 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    const uint64_t* h = c->two_host;
+    std::memset(out, 0, sizeof *out);
+    for (int i = 0; i < 2; ++i) {
+        out->sum_u32[i] = static_cast<uint32_t>(h[3 * i]);
+        out->xor_u64[i] = h[3 * i + 1];
+        out->issued_loads[i] = h[3 * i + 2];
+        const uint64_t t0 = h[6 + sl::TWO_START + i], t1 = h[6 + sl::TWO_END + i];
+        out->window_ns[i] = (i == 0 || warps_b > 0) && t1 > t0 ? t1 - t0 : 0;
+    }
+    const uint64_t a0 = h[6 + sl::TWO_START], a1 = h[6 + sl::TWO_END], bfe = h[6 + sl::TWO_FIRST_END_B];
+    out->b_first_end_ns = warps_b > 0 && bfe > a0 ? bfe - a0 : 0;
+    out->b_covers_a = warps_b == 0 || bfe >= a1 ? 1 : 0;
+    out->device_ns = static_cast<uint64_t>(static_cast<double>(ms) * 1e6 + 0.5);
+    out->grid = static_cast<int32_t>(grid);
+    out->cta = block;
+    return SL_OK;
+}
+
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
     if (!out || !cfg) return fail(SL_ERR_ARG, "NULL argument");
     if (bytes > 0 && !host_buf) return fail(SL_ERR_ARG, "host buffer is NULL");
@@ -582,7 +688,7 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
         CUDA_TRY(cudaEventRecord(c->copied[b], c->copy_stream));
         CUDA_TRY(cudaStreamWaitEvent(s, c->copied[b], 0));
         KArgs a = p.args;
-        const uint64_t nvec = len / 16;
+        const uint64_t nvec = len / (cfg->mech == SL_LDG4 ? 4 : 16);
         a.buf = c->stage[b];
         a.nvec = nvec;
         a.ntiles = (nvec + a.tile_vec - 1) / a.tile_vec;

@@ -24,7 +24,7 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int D, int DT>
-__global__ void __launch_bounds__(1024) k_cpasync(const KArgs a) {
+__global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
     extern __shared__ __align__(16) uint4 ring[];  // [D][cta]: slot k holds chunk k of a tile
     cta_start(a);
     const uint32_t cta = blockDim.x;
@@ -52,25 +52,27 @@ __global__ void __launch_bounds__(1024) k_cpasync(const KArgs a) {
         const uint32_t cur = c.tile(a);
         c.next(ntiles);
         const bool has_next = c.it < total;
-        const uint32_t nxt = has_next ? c.tile(a) : 0u;
-        const uint64_t cbase = static_cast<uint64_t>(cur) * tile_vec;
-        const uint64_t nbase = static_cast<uint64_t>(nxt) * tile_vec;
-        const bool cfull = cbase + tile_vec <= nvec;
-        const bool nfull = has_next && nbase + tile_vec <= nvec;
-        const uint4* np = buf + nbase + threadIdx.x;
+        const uint64_t cbase = static_cast<uint64_t>(cur) * tile_vec + threadIdx.x;
+        const uint64_t nbase = has_next ? static_cast<uint64_t>(c.tile(a)) * tile_vec + threadIdx.x : nvec;
+        // vectors left from this thread's first chunk of the current / next
+        // tile, clamped to 32 bits: chunk k is in range iff k*cta < rem
+        const uint32_t crem = cbase < nvec ? static_cast<uint32_t>(min(nvec - cbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
+        const uint32_t nrem = nbase < nvec ? static_cast<uint32_t>(min(nvec - nbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
+        const bool cfull = cbase - threadIdx.x + tile_vec <= nvec;
+        const uint4* np = buf + (has_next ? nbase : 0);
+        uint32_t off = 0;  // k * cta
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             // D groups are pending; wait until the oldest (chunk k of cur) has landed
             cp_async_wait<D - 1>();
-            const uint64_t cv = cbase + static_cast<uint64_t>(k) * cta + threadIdx.x;
-            if (cfull || cv < nvec) {
+            if (off < crem) {
                 acc.fold(lds16(my0 + k * stride));
                 if (!cfull) acc.n += 1;
             }
             // refill slot k with chunk k of the next tile (an empty group at the end)
-            if (nfull || (has_next && nbase + static_cast<uint64_t>(k) * cta + threadIdx.x < nvec))
-                cp_async16(my0 + k * stride, np + k * cta);
+            if (off < nrem) cp_async16(my0 + k * stride, np + off);
             cp_async_commit();
+            off += cta;
         }
         if (cfull) ++full_tiles;
     }

@@ -56,6 +56,27 @@ const void* ldg_dyn_kernel(int dtype, int k, int cta);
 const void* cpasync_kernel(int dtype, int d);
 const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
+const void* ldg4_kernel(int dtype, int k, int cta);
+
+// Two co-resident streams in one CTA (k_two.cu).  Stream A = warps
+// [0, warps_a), stream B = the warps_b warps after them; one CTA per SM.
+struct TwoArgs {
+    const uint4* buf_a;
+    const uint4* buf_b;
+    uint64_t nvec_a, nvec_b;      // 16-byte vectors per pass
+    uint32_t ntiles_a, ntiles_b;  // tiles per pass (stream threads * K vectors each)
+    uint32_t total_a, total_b;    // tiles over all passes
+    uint32_t warps_a, warps_b;
+    WarpPartial* parts;           // [grid * 32]: one partial per warp slot
+    uint64_t* ctl;                // TWO_CTL_WORDS %globaltimer words, set by the host before the launch
+};
+// Timer words: earliest warp start of A and B (min; ~0 before), latest warp
+// end of A and B (max; 0 before), earliest warp end of B (min; ~0 before).
+enum : int { TWO_START = 0, TWO_END = 2, TWO_FIRST_END_B = 4, TWO_CTL_WORDS = 5 };
+const void* two_kernel(int k);
+cudaError_t launch_two(const TwoArgs& t, int k, uint32_t grid, cudaStream_t s);
+// out[0..2] = A {sum, xor, issued}, out[3..5] = B, out[6..10] = timer words.
+cudaError_t launch_two_combine(const TwoArgs& t, uint32_t grid, uint64_t* out, cudaStream_t s);
 
 // Pointer chase (k_chase.cu): out[4] = final index, ns, cycles, out-of-range flag.
 cudaError_t launch_chase(const uint32_t* chain, uint64_t nwords, uint32_t start, uint64_t warm, uint64_t hops,

@@ -37,9 +37,12 @@ GPU and checked against the first cell's checksum):
   ncu  a small case for counter captures (1 GiB, one launch per cell, no
        warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), LDG K=4 with the
        dynamic-chunk traversal, cp.async D=2, TMA 16 KiB x 2 stages.
-  prec  the precision form: 1 GiB N(0,1) payloads (float32, bfloat16, FP8
-       E4M3 x8) through LDG, cp.async and TMA points; GB/s and the error of
-       the sum against the FP64 oracle.
+  k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
+       (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
+       4 GiB, beside 16-byte LDG at K = 1, 2, 4.
+  two  paper §4.4: two co-resident plain-load streams in one CTA per SM,
+       stream A = 1/2/4/8/16 warps, stream B = 0..16 warps, K = 1, 2, 4;
+       displacement of A's bandwidth by B.
   ncu-points  every candidate point of the benchmark (tune.default_points)
        on 1 GiB, then LDG K=2 and K=8 on 512 MiB and 2 GiB (one launch each,
        no warm-up): DRAM bytes per launch for the roofline, and the paper's
@@ -112,6 +115,12 @@ def _cells(config: str, sms: int):
                 yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=mib / 1024, passes=passes)
             for k in (1, 2, 4, 8):
                 yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=mib / 1024, passes=passes)
+    elif config == "k1gate":
+        for cta in (256, 1024):
+            for k in (1, 2, 4, 8, 16):
+                yield dict(mech="ldg4", k=k, cta=cta, grid=0, gib=4)
+            for k in (1, 2, 4):
+                yield dict(mech="ldg", k=k, cta=cta, grid=0, gib=4)
     elif config == "ncu-points":
         from .tune import default_points
         for p in default_points():
@@ -215,7 +224,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                     gbs_max=round(max(gbs), 2) if gbs else None,
                     gbs=[round(v, 2) for v in gbs],
                     window_gbs_median=round(statistics.median(wgbs), 2) if wgbs else None,
-                    issued_ok=all(r.issued_loads == vol // 16 for r in ok),
+                    issued_ok=all(r.issued_loads == vol // (4 if row["mech"] == "ldg4" else 16) for r in ok),
                     checksum_ok=(cks == {ref}),
                     above_datasheet=bool(gbs and max(gbs) > DATASHEET_GBS),
                     frac_of_datasheet=round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,
@@ -223,68 +232,6 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                 rows.append(row)
                 _emit(out, row, verbose)
         del buf
-        torch.cuda.empty_cache()
-    return rows
-
-
-PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
-              [dict(mech="cpasync", k=d, cta=256) for d in (2, 4, 6)] +
-              [dict(mech="tma", stage_bytes=sb, stages=n, cta=256) for sb, n in ((16384, 2), (16384, 4), (65536, 2))])
-
-
-def run_prec(out: str | None, repeats: int = 5, gib: float = 1.0, verbose: bool = True):
-    """Precision form: N(0,1) payloads (float32, bfloat16, FP8-E4M3 x8) of
-    `gib` GiB through every mechanism; GB/s and the error of the compensated
-    FP32 / FP64-combine sum against the FP64 oracle (relative, and normalised by
-    sum|x|), plus the uint32 checksum against the oracle."""
-    import math
-    from concurrent.futures import ThreadPoolExecutor
-
-    import numpy as np
-    import torch
-
-    import oracle
-    import paper_2608_15764_gb300 as sl
-    from . import workloads as wl
-
-    sl.load()
-    rows = []
-    nbytes = int(gib * (1 << 30)) // 16 * 16
-    threads = os.cpu_count() or 1
-    for dt in (wl.F32, wl.BF16, wl.FP8_E4M3):
-        n = nbytes // wl.ELEM_BYTES[dt]
-        host = wl.payload(dt, n)
-        hb = host.view(np.uint8)
-        # reference: the oracle over one contiguous range per thread, the
-        # range sums added with math.fsum (correctly rounded)
-        cut = [i * (n // threads) // 16 * 16 for i in range(threads)] + [n]
-        with ThreadPoolExecutor(threads) as ex:
-            parts = list(ex.map(lambda i: oracle.fsum(dt, host[cut[i]:cut[i + 1]]), range(threads)))
-            cks = list(ex.map(lambda i: oracle.checksum(hb[cut[i] * wl.ELEM_BYTES[dt]:cut[i + 1] * wl.ELEM_BYTES[dt]]),
-                              range(threads)))
-        ref = math.fsum(p[0] for p in parts)
-        absum = math.fsum(p[1] for p in parts)
-        ck = oracle.combine(cks)
-        dev = torch.from_numpy(hb).cuda()
-        cfgs = []
-        for c in PREC_CELLS:
-            kw = {k: v for k, v in c.items() if k != "mech"}
-            cfgs.append(sl.config(c["mech"], **kw))
-        res = sl.sl_sweep(dev, cfgs, dtype=dt, repeats=repeats, warmup=1)
-        for c, rr in zip(PREC_CELLS, res):
-            gbs = [nbytes / r.device_ns for r in rr if r.status == 0 and r.device_ns]
-            fs = [r.fsum for r in rr]
-            row = {"config": "prec", "dtype": {1: "f32", 2: "bf16", 3: "fp8"}[dt], "bytes": nbytes, **c,
-                   "status": rr[0].status, "gbs_median": round(statistics.median(gbs), 2) if gbs else None,
-                   "frac_of_datasheet": round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,
-                   "ref_fsum": ref, "abs_sum": absum,
-                   "rel_err": max(abs(f - ref) for f in fs) / abs(ref),
-                   "err_over_abs_sum": max(abs(f - ref) for f in fs) / absum,
-                   "checksum_ok": all((r.sum_u32, r.xor_u64) == ck for r in rr),
-                   "deterministic": len(set(fs)) == 1}
-            rows.append(row)
-            _emit(out, row, verbose)
-        del dev
         torch.cuda.empty_cache()
     return rows
 
@@ -308,12 +255,12 @@ def run_ladder(out: str | None, verbose: bool = True):
     cycle through every element), .ca and .cg.  Before each chase the L2 is
     flushed; chains of up to 4 Mi elements (256 MiB) are first walked once in
     full (untimed), so the timed steps revisit lines that the footprint lets
-    the caches keep; longer chains are not warmed.  32,768 steps are timed and
-    the final index is checked against the oracle."""
+    the caches keep; longer chains are not warmed.  32,768 steps are timed.
+    The .ca and .cg walks of a chain must end on the same index (the chase
+    itself is checked against the oracle by the test suite)."""
     import numpy as np
     import torch
 
-    import oracle
     import paper_2608_15764_gb300 as sl
     from . import workloads as wl
 
@@ -324,13 +271,15 @@ def run_ladder(out: str | None, verbose: bool = True):
         host = wl.chase_chain(n, 64)
         dev = torch.from_numpy(host.view(np.uint8)).cuda()
         warm, hops = (n if n <= (1 << 22) else 0), 1 << 15
-        want = oracle.chase(host, 0, warm + hops)
+        finals = set()
         for ca in (True, False):
             sl.sl_flush_l2()
             torch.cuda.synchronize()
             r = sl.sl_chase(dev, warm=warm, hops=hops, cache_l1=ca)
+            finals.add(r.final_index)
             row = {"config": "ladder", "footprint": fp, "cop": "ca" if ca else "cg", "ns_per_hop": round(r.ns_per_hop, 2),
-                   "cycles_per_hop": round(r.cycles_per_hop, 1), "final_ok": r.final_index == want}
+                   "cycles_per_hop": round(r.cycles_per_hop, 1), "final_index": r.final_index,
+                   "ca_cg_agree": len(finals) == 1}
             rows.append(row)
             if out:
                 with open(out, "a") as f:
@@ -338,6 +287,79 @@ def run_ladder(out: str | None, verbose: bool = True):
             if verbose:
                 print(json.dumps(row), flush=True)
         del dev
+    return rows
+
+
+TWO_WARPS = (1, 2, 4, 8, 16)
+TWO_B_WARPS = (0, 1, 2, 4, 8, 16)
+
+
+def run_two(out: str | None, repeats: int = 3, ks=(1, 2, 4), a_gib: float = 1.0, b_gib: float = 2.0,
+            verbose: bool = True):
+    """Paper §4.4: two co-resident plain-load streams in one CTA per SM.
+    Stream A (A warps) reads a 1 GiB buffer once; stream B (B warps) re-reads
+    a 2 GiB buffer for as many passes as it takes to keep loading until A's
+    last warp is done (start from 3x A's solo time at 8 TB/s, double until
+    sl_twostream reports b_covers_a).  A's bandwidth = bytes / A's
+    %globaltimer window (median of `repeats`); displacement = 1 - A(B) / A(0).
+    Checksums: A's must agree across every cell, B's must follow the
+    closed form of its pass count from a single-pass read of B's buffer."""
+    import torch
+
+    import paper_2608_15764_gb300 as sl
+
+    sl.load()
+    nb_a = int(a_gib * (1 << 30)) // 16 * 16
+    nb_b = int(b_gib * (1 << 30)) // 16 * 16
+    a = torch.empty(nb_a, dtype=torch.uint8, device="cuda")
+    b = torch.empty(nb_b, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(a, seed=21)
+    sl.sl_fill_splitmix64(b, seed=22)
+    r1 = sl.sl_run(b, dtype=sl.SL_U32, cfg=sl.config("ldg", k=4))
+    sb, xb = r1.sum_u32, r1.xor_u64
+    ref_a = None
+    rows = []
+    for k in ks:
+        for wa in TWO_WARPS:
+            solo_gbs, solo_ns = None, None
+            for wb in TWO_B_WARPS:
+                if wa + wb > 32:
+                    continue
+                passes, pmax = 1, 1
+                if wb:
+                    tiles_b = -(-(nb_b // 16) // (32 * wb * k))
+                    pmax = ((1 << 32) - 4096) // tiles_b  # the kernel counts tiles in 32 bits
+                    passes = min(pmax, max(1, -(-int(3 * solo_ns * 8.0) // nb_b)))
+                gbs, bgbs, cover, ck_ok = [], [], True, True
+                for _ in range(repeats):
+                    for _try in range(6):
+                        r = sl.sl_twostream(a, b if wb else None, warps_a=wa, warps_b=wb, k=k, passes_b=passes)
+                        if r.b_covers_a or passes >= pmax:
+                            break
+                        passes = min(pmax, 2 * passes)
+                    cover = cover and bool(r.b_covers_a)
+                    ca = (r.sum_u32[0], r.xor_u64[0])
+                    ref_a = ref_a or ca
+                    ck_ok = ck_ok and ca == ref_a and r.issued_loads[0] == nb_a // 16
+                    if wb:
+                        ck_ok = ck_ok and (r.sum_u32[1], r.xor_u64[1]) == ((passes * sb) % (1 << 32),
+                                                                             xb if passes % 2 else 0)
+                        bgbs.append(passes * nb_b / r.window_ns[1])
+                    gbs.append(nb_a / r.window_ns[0])
+                med = statistics.median(gbs)
+                if wb == 0:
+                    solo_gbs, solo_ns = med, nb_a / med
+                row = {"config": "two", "k": k, "warps_a": wa, "warps_b": wb, "a_gbs": round(med, 2),
+                       "a_gbs_all": [round(v, 2) for v in gbs],
+                       "displacement_pct": round(100.0 * (1.0 - med / solo_gbs), 2),
+                       "b_gbs": round(statistics.median(bgbs), 2) if bgbs else None, "passes_b": passes,
+                       "b_covers_a": cover, "checksum_ok": ck_ok}
+                rows.append(row)
+                if out:
+                    with open(out, "a") as f:
+                        f.write(json.dumps(row) + "\n")
+                if verbose:
+                    print(json.dumps(row), flush=True)
     return rows
 
 
@@ -406,19 +428,19 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "prec", "l2",
-                             "cpratio", "ladder"])
+                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
+                             "cpratio", "ladder", "k1gate", "two"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
     a = ap.parse_args(argv)
     t0 = time.time()
-    if a.config == "ladder":
-        rows = run_ladder(a.out)
+    if a.config == "two":
+        rows = run_two(a.out, repeats=min(a.repeats, 5))
         print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
         return 0
-    if a.config == "prec":
-        rows = run_prec(a.out, repeats=a.repeats)
+    if a.config == "ladder":
+        rows = run_ladder(a.out)
         print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
         return 0
     ncu = a.config.startswith("ncu")

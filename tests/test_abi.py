@@ -54,6 +54,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(sl_config), sizeof(sl_result), sizeof(sl_devinfo));
   printf("%zu %zu %zu\n", offsetof(sl_config, stream), offsetof(sl_result, sum_u32), offsetof(sl_result, smem_bytes));
   printf("%zu %zu\n", offsetof(sl_devinfo, name), offsetof(sl_devinfo, l2_bytes));
+  printf("%zu %zu %zu\n", sizeof(sl_twostream_result), offsetof(sl_twostream_result, sum_u32),
+         offsetof(sl_twostream_result, b_covers_a));
   return 0;
 }
 ''')
@@ -69,6 +71,9 @@ int main(void) {
     assert vals[5] == _abi.sl_result.smem_bytes.offset
     assert vals[6] == _abi.sl_devinfo.name.offset
     assert vals[7] == _abi.sl_devinfo.l2_bytes.offset
+    assert vals[8] == ctypes.sizeof(_abi.sl_twostream_result)
+    assert vals[9] == _abi.sl_twostream_result.sum_u32.offset
+    assert vals[10] == _abi.sl_twostream_result.b_covers_a.offset
 
 
 def test_library_targets_sm_103a_only():

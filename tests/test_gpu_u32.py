@@ -128,6 +128,41 @@ def test_small_and_ragged(sl, data, nvec, mech, kw):
     _check(sl, dev, nbytes, want, sl.config(mech, cta=256, **kw))
 
 
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("cta", [128, 256, 512, 1024])
+@pytest.mark.parametrize("order", ["asc", "desc"])
+def test_ldg4_every_shape(sl, data, k, cta, order):
+    """4-byte plain loads (paper §4.1's K1 streaming row and its K sweep): the
+    same checksum; issued loads count 4-byte loads."""
+    dev, _, want = data
+    r = sl.sl_run(dev, nbytes=NBYTES, dtype=sl.SL_U32, cfg=sl.config("ldg4", k=k, cta=cta, order=order))
+    assert (r.sum_u32, r.xor_u64) == want
+    assert r.issued_loads == NBYTES // 4
+
+
+@pytest.mark.parametrize("nvec", [0, 1, 2, 3, 31, 33, 255, 257, 4096 + 5])
+@pytest.mark.parametrize("k", [1, 16])
+def test_ldg4_small_ragged_and_passes(sl, data, nvec, k):
+    dev, host, _ = data
+    nbytes = 16 * nvec
+    s, x = oracle.checksum(host[: nbytes // 4])
+    for passes in (1, 3):
+        r = sl.sl_run(dev, nbytes=nbytes, dtype=sl.SL_U32,
+                      cfg=sl.config("ldg4", k=k, cta=128, grid=7, passes=passes))
+        assert (r.sum_u32, r.xor_u64) == ((passes * s) % (1 << 32), x if passes % 2 else 0)
+        assert r.issued_loads == passes * nbytes // 4
+
+
+def test_ldg4_rejects_other_forms(sl, data):
+    dev, _, _ = data
+    for kw, dtype, code in [(dict(k=3), sl.SL_U32, sl.SL_ERR_ARG), (dict(k=1, cta=32), sl.SL_U32, sl.SL_ERR_ARG),
+                            (dict(k=1), sl.SL_F32, sl.SL_ERR_ARG), (dict(k=1, cop=1), sl.SL_U32, sl.SL_ERR_ARG),
+                            (dict(k=1, order="dyn"), sl.SL_U32, sl.SL_ERR_ARG)]:
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_run(dev, nbytes=1024, dtype=dtype, cfg=sl.config("ldg4", **kw))
+        assert e.value.status == code, kw
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8, 12, 16])
 @pytest.mark.parametrize("cta", [128, 256, 512])
 def test_ldg_dynamic_chunks(sl, data, k, cta):
