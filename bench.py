@@ -239,7 +239,7 @@ def run_reference(a):
 def run_ours(a):
     import torch
     import paper_2608_15764_gb300 as sl
-    from paper_2608_15764_gb300 import tune
+    from paper_2608_15764_gb300 import replicas, tune
 
     rank, world, local = _dist()
     if not torch.cuda.is_available():
@@ -270,9 +270,7 @@ def run_ours(a):
         choice = [points.index(best)]
     else:
         choice = [0]
-    if dist:
-        dist.broadcast_object_list(choice, src=0)
-    best = points[choice[0]]
+    best = points[replicas.broadcast_choice(choice[0], dist)]
     cfg = best.cfg()
 
     # ---- timed steps
@@ -299,18 +297,18 @@ def run_ours(a):
     clk = clocks.stop() if rank == 0 else None
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)]
     total_ms = ev[0].elapsed_time(ev[a.steps])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nbytes * a.steps / (total_ms * 1e6)
+    total_ms = replicas.max_over_ranks(total_ms, dist, device="cuda")
+    value = replicas.job_gbs(nbytes, a.steps, world, total_ms)
 
-    # results of every timed step must agree
+    # results of every timed step must agree, and so must the ranks (each
+    # streams an identical buffer)
     raw = dev_out.cpu().numpy().tobytes()
     rb = sl.RESULT_BYTES
     res = [sl.sl_result.from_buffer_copy(raw[rb * i:rb * (i + 1)]) for i in range(a.warmup + a.steps)]
     ck = {(r.sum_u32, r.xor_u64, r.issued_loads, r.status) for r in res}
     consistent = len(ck) == 1 and res[0].issued_loads == nbytes // 16 and res[0].status == 0
+    per_rank = replicas.gather_results(res[-1].sum_u32, res[-1].xor_u64, res[-1].issued_loads, dist, device="cuda")
+    ranks_agree = len(set(per_rank)) == 1
 
     if rank != 0:
         if dist:
@@ -380,7 +378,8 @@ def run_ours(a):
                 "modes": [{k: v for k, v in e.items() if k != "result"} for e in e2e_all]},
         "gpu_launches": a.steps,
         "clocks": clk,
-        "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent)},
+        "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent),
+                   "ranks_agree": bool(ranks_agree)},
         "curves": [p.as_dict() for p in points],
         "device": {k: info[k] for k in ("name", "sm_count", "l2_bytes", "cc_major", "cc_minor")},
     }

@@ -35,8 +35,8 @@ GPU and checked against the first cell's checksum):
   primary  the paper's primary cell shape (§4.2: one CTA of 32 warps per SM,
        .cg, 16-byte loads), K in {1,2,4,8}, on 4 GiB.
   ncu  a small case for counter captures (1 GiB, one launch per cell, no
-       warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), LDG K=4 with the
-       dynamic-chunk traversal, cp.async D=2, TMA 16 KiB x 2 stages.
+       warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), LDG K=4 and K=12
+       with the dynamic-chunk traversal, cp.async D=2, TMA 16 KiB x 2 stages.
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
@@ -136,6 +136,7 @@ def _cells(config: str, sms: int):
         yield dict(mech="ldg", k=2, cta=256, grid=4 * sms, gib=1)
         yield dict(mech="ldg", k=8, cta=256, grid=4 * sms, gib=1)
         yield dict(mech="ldg", k=4, cta=256, grid=0, trav=2, gib=1)
+        yield dict(mech="ldg", k=12, cta=256, grid=0, trav=2, gib=1)
         yield dict(mech="cpasync", k=2, cta=256, grid=0, gib=1)
         yield dict(mech="tma", stage_bytes=16384, stages=2, cta=256, grid=0, gib=1)
     else:
@@ -299,8 +300,8 @@ def run_two(out: str | None, repeats: int = 3, ks=(1, 2, 4), a_gib: float = 1.0,
     """Paper §4.4: two co-resident plain-load streams in one CTA per SM.
     Stream A (A warps) reads a 1 GiB buffer once; stream B (B warps) re-reads
     a 2 GiB buffer for as many passes as it takes to keep loading until A's
-    last warp is done (start from 3x A's solo time at 8 TB/s, double until
-    sl_twostream reports b_covers_a).  A's bandwidth = bytes / A's
+    last warp is done (start from the pass count of the previous B width,
+    double until sl_twostream reports b_covers_a).  A's bandwidth = bytes / A's
     %globaltimer window (median of `repeats`); displacement = 1 - A(B) / A(0).
     Checksums: A's must agree across every cell, B's must follow the
     closed form of its pass count from a single-pass read of B's buffer."""
@@ -321,7 +322,7 @@ def run_two(out: str | None, repeats: int = 3, ks=(1, 2, 4), a_gib: float = 1.0,
     rows = []
     for k in ks:
         for wa in TWO_WARPS:
-            solo_gbs, solo_ns = None, None
+            solo_gbs, prev_passes = None, 1
             for wb in TWO_B_WARPS:
                 if wa + wb > 32:
                     continue
@@ -329,7 +330,7 @@ def run_two(out: str | None, repeats: int = 3, ks=(1, 2, 4), a_gib: float = 1.0,
                 if wb:
                     tiles_b = -(-(nb_b // 16) // (32 * wb * k))
                     pmax = ((1 << 32) - 4096) // tiles_b  # the kernel counts tiles in 32 bits
-                    passes = min(pmax, max(1, -(-int(3 * solo_ns * 8.0) // nb_b)))
+                    passes = min(pmax, prev_passes)
                 gbs, bgbs, cover, ck_ok = [], [], True, True
                 for _ in range(repeats):
                     for _try in range(6):
@@ -348,7 +349,8 @@ def run_two(out: str | None, repeats: int = 3, ks=(1, 2, 4), a_gib: float = 1.0,
                     gbs.append(nb_a / r.window_ns[0])
                 med = statistics.median(gbs)
                 if wb == 0:
-                    solo_gbs, solo_ns = med, nb_a / med
+                    solo_gbs = med
+                prev_passes = passes
                 row = {"config": "two", "k": k, "warps_a": wa, "warps_b": wb, "a_gbs": round(med, 2),
                        "a_gbs_all": [round(v, 2) for v in gbs],
                        "displacement_pct": round(100.0 * (1.0 - med / solo_gbs), 2),
