@@ -359,7 +359,7 @@ def run_ours(a):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "bytes": nbytes, "choice": best.label(),
+        "config": {"workload": WORKLOAD, "bytes": nbytes, "choice": best.label(), "choice_spec": best.spec(),
                    "grid": best.grid_used, "resident_per_sm": best.resident,
                    "l2": "inputs larger than L2 (4 GiB vs 129 MB): no flush between steps",
                    "parallelism": f"replicas x{world} (one buffer per GPU)"},

@@ -75,10 +75,15 @@ typedef enum { SL_U32 = 0, SL_F32 = 1, SL_BF16 = 2, SL_FP8_E4M3 = 3 } sl_dtype;
  * 4-byte ld.global.cg per thread per iteration (the paper's gate is K = 1);
  * uint32 payloads, K in {1,2,4,8,16}, cta 128/256/512/1024, SL_COP_CG, no
  * SL_DYN.  Its issued_loads counts 4-byte loads: passes*bytes/4. */
-typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2, SL_LDSTS = 3, SL_LDG4 = 4 } sl_mech;
+/* SL_LDG32: the 32-byte width (256-bit ld.global.cg.v8.u32, sm_100 class):
+ * K independent 32-byte loads per thread per iteration, K in {1,2,3,4,6,8},
+ * cta 128/256/512, every dtype, SL_ASC / SL_DESC / SL_DYN, SL_COP_CG; the
+ * buffer must be 32-byte aligned (SL_ERR_ALIGN).  issued_loads counts loads:
+ * passes * ceil(bytes/32) (a final 16-byte remainder is one 16-byte load). */
+typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2, SL_LDSTS = 3, SL_LDG4 = 4, SL_LDG32 = 5 } sl_mech;
 /* Traversal of the buffer by the CTAs.  SL_ASC / SL_DESC: CTA b takes tiles
  * b, b+grid, ... from the first (or last) tile on (the paper's layout).
- * SL_DYN (LDG only): CTAs claim contiguous chunks of about 1 MiB from an
+ * SL_DYN (SL_LDG and SL_LDG32): CTAs claim contiguous chunks of about 1 MiB from an
  * atomic counter; integer results are exact, float sums meet the same bound
  * but are not bit-reproducible between runs. */
 typedef enum { SL_ASC = 0, SL_DESC = 1, SL_DYN = 2 } sl_order;
@@ -98,6 +103,7 @@ typedef struct sl_config {
                             iteration, 1..16.  SL_CPASYNC: D = commit groups in
                             flight per thread, 1..16.  SL_LDSTS: G = loads per
                             thread staged through shared memory, 1..16.
+                            SL_LDG4 / SL_LDG32: K loads of 4 / 32 bytes.
                             SL_TMA: ignored. */
     int32_t stage_bytes; /* SL_TMA: bytes per ring stage, 4096, 16384 or 65536 */
     int32_t stages;      /* SL_TMA: ring depth, 2..8 */
@@ -129,7 +135,8 @@ typedef struct sl_config {
 typedef struct sl_result {
     uint64_t xor_u64;         /* XOR of the little-endian uint64 words read */
     uint64_t issued_loads;    /* 16-byte logical loads folded; = passes*bytes/16
-                                 (SL_LDG4: 4-byte loads, passes*bytes/4) */
+                                 (SL_LDG4: 4-byte loads, passes*bytes/4;
+                                 SL_LDG32: passes*ceil(bytes/32)) */
     uint64_t device_ns;       /* CUDA-event time of the load kernel (sl_run);
                                  of the whole call (sl_run_host); 0 (sl_enqueue) */
     uint64_t window_ns;       /* %globaltimer: first CTA start to last CTA end */

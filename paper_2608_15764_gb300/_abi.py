@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "SL_OK", -1: "SL_ERR_ARG", -2: "SL_ERR_ALIGN", -3: "SL_ERR_IN
 
 # enums
 SL_U32, SL_F32, SL_BF16, SL_FP8_E4M3 = 0, 1, 2, 3
-SL_LDG, SL_CPASYNC, SL_TMA, SL_LDSTS, SL_LDG4 = 0, 1, 2, 3, 4
+SL_LDG, SL_CPASYNC, SL_TMA, SL_LDSTS, SL_LDG4, SL_LDG32 = 0, 1, 2, 3, 4, 5
 SL_ASC, SL_DESC, SL_DYN = 0, 1, 2
 SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256 = 0, 1, 2
 SL_MAX_K, SL_MAX_D, SL_MIN_STAGES, SL_MAX_STAGES = 16, 16, 2, 8

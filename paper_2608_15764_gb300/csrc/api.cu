@@ -217,8 +217,8 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (cfg->order != SL_ASC && cfg->order != SL_DESC && cfg->order != SL_DYN)
         return fail(SL_ERR_ARG, "bad order %d", cfg->order);
     const bool dyn = cfg->order == SL_DYN;
-    if (dyn && (cfg->mech != SL_LDG || cfg->cop != SL_COP_CG))
-        return fail(SL_ERR_ARG, "the SL_DYN traversal is implemented for the LDG mechanism with SL_COP_CG");
+    if (dyn && ((cfg->mech != SL_LDG && cfg->mech != SL_LDG32) || cfg->cop != SL_COP_CG))
+        return fail(SL_ERR_ARG, "the SL_DYN traversal is implemented for SL_LDG / SL_LDG32 with SL_COP_CG");
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
     const int cta = cfg->cta;
     if (cta < 32 || cta > 1024 || (cta & 31)) return fail(SL_ERR_ARG, "cta %d not a multiple of 32 in 32..1024", cta);
@@ -252,6 +252,20 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
         p->block = cta;
         p->smem = 0;
         tile_vec = static_cast<uint64_t>(cta) * cfg->k;  // in 4-byte words
+        p->warps = cta / 32;
+        break;
+    case SL_LDG32:
+        if ((reinterpret_cast<uintptr_t>(buf) & 31u) != 0)
+            return fail(SL_ERR_ALIGN, "SL_LDG32 needs a 32-byte aligned buffer");
+        if (cfg->cop != SL_COP_CG) return fail(SL_ERR_ARG, "SL_LDG32 has the SL_COP_CG flavour only");
+        p->fn = sl::ldg32_kernel(dtype, cfg->k, cta, dyn);
+        if (!p->fn)
+            return fail(SL_ERR_ARG, "no 32-byte LDG kernel for K %d, cta %d (K in {1,2,3,4,6,8}, cta 128/256/512)",
+                        cfg->k, cta);
+        p->block = cta;
+        p->smem = 0;
+        tile_vec = static_cast<uint64_t>(cta) * cfg->k;  // in 32-byte units
+        if (dyn) tile_vec *= std::max<uint64_t>(1, (DYN_CHUNK_VEC / 2) / tile_vec);
         p->warps = cta / 32;
         break;
     case SL_CPASYNC:
@@ -296,6 +310,9 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if ((cfg->mech == SL_LDG || cfg->mech == SL_LDSTS) && fi->regs < 4 * cfg->k + 16)
         return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d loads in flight at cta %d",
                     fi->regs, cfg->k, cta);
+    if (cfg->mech == SL_LDG32 && fi->regs < 8 * cfg->k + 16)
+        return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d 32-byte loads in flight at cta %d",
+                    fi->regs, cfg->k, cta);
     if (cfg->mech == SL_LDG4 && fi->regs < cfg->k + 16)
         return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d 4-byte loads in flight at cta %d",
                     fi->regs, cfg->k, cta);
@@ -306,8 +323,11 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (rc) return rc;
     if (p->resident < 1) return fail(SL_ERR_INFEASIBLE, "configuration has zero occupancy");
 
-    const uint64_t nvec = bytes / (cfg->mech == SL_LDG4 ? 4 : 16);  // load units: 16-byte vectors or words
-    const uint64_t ntiles = (nvec + tile_vec - 1) / tile_vec;
+    // nvec: 16-byte vectors (4-byte words for SL_LDG4); units: what a tile counts
+    // (SL_LDG32: 32-byte units, a final half unit included)
+    const uint64_t nvec = bytes / (cfg->mech == SL_LDG4 ? 4 : 16);
+    const uint64_t units = cfg->mech == SL_LDG32 ? (nvec + 1) / 2 : nvec;
+    const uint64_t ntiles = (units + tile_vec - 1) / tile_vec;
     int64_t grid = cfg->grid;
     if (grid <= 0) grid = static_cast<int64_t>(std::min(4, p->resident)) * c->info.sm_count;
     if (grid > MAX_GRID) return fail(SL_ERR_ARG, "grid %lld > %lld", (long long)grid, (long long)MAX_GRID);
@@ -689,9 +709,10 @@ int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_co
         CUDA_TRY(cudaStreamWaitEvent(s, c->copied[b], 0));
         KArgs a = p.args;
         const uint64_t nvec = len / (cfg->mech == SL_LDG4 ? 4 : 16);
+        const uint64_t units = cfg->mech == SL_LDG32 ? (nvec + 1) / 2 : nvec;
         a.buf = c->stage[b];
         a.nvec = nvec;
-        a.ntiles = (nvec + a.tile_vec - 1) / a.tile_vec;
+        a.ntiles = (units + a.tile_vec - 1) / a.tile_vec;
         a.total = a.ntiles * passes;
         a.parts = c->parts + i * per_parts;
         a.window = sl::ctrl_window(c->err);

@@ -57,6 +57,7 @@ const void* cpasync_kernel(int dtype, int d);
 const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
 const void* ldg4_kernel(int dtype, int k, int cta);
+const void* ldg32_kernel(int dtype, int k, int cta, bool dyn);
 
 // Two co-resident streams in one CTA (k_two.cu).  Stream A = warps
 // [0, warps_a), stream B = the warps_b warps after them; one CTA per SM.

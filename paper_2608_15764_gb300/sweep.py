@@ -86,6 +86,9 @@ def _cells(config: str, sms: int):
             yield dict(mech="ldg", k=k, cta=256, grid=0, gib=4)
         for k in (1, 2, 3, 4, 6, 8, 12, 16):
             yield dict(mech="ldg", k=k, cta=256, grid=0, trav=2, gib=4)
+        for trav in (0, 2):
+            for k in (1, 2, 3, 4, 6, 8):
+                yield dict(mech="ldg32", k=k, cta=256, grid=0, trav=trav, gib=4)
         for d in range(1, 9):
             yield dict(mech="cpasync", k=d, cta=256, grid=0, gib=4)
         for sb in (4096, 16384, 65536):
@@ -122,12 +125,12 @@ def _cells(config: str, sms: int):
             for k in (1, 2, 4):
                 yield dict(mech="ldg", k=k, cta=cta, grid=0, gib=4)
     elif config == "ncu-points":
-        from .tune import default_points
+        from .tune import MECH_NAMES, default_points
         for p in default_points():
             if p.mech == 2:
                 yield dict(mech="tma", stage_bytes=p.stage_bytes, stages=p.stages, cta=p.cta, grid=0, gib=1)
             else:
-                yield dict(mech="ldg" if p.mech == 0 else "cpasync", k=p.k, cta=p.cta, grid=0, cop=p.cop,
+                yield dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop,
                            trav=p.order, gib=1)
         for gib in (0.5, 2):
             for k in (2, 8):
@@ -141,6 +144,17 @@ def _cells(config: str, sms: int):
         yield dict(mech="tma", stage_bytes=16384, stages=2, cta=256, grid=0, gib=1)
     else:
         raise ValueError(config)
+
+
+def _expected_loads(mech: str, nbytes: int, passes: int) -> int:
+    """Loads a launch issues under exact fixed work: 16-byte loads, 4-byte
+    loads (ldg4), or 32-byte loads plus one 16-byte load for a final half
+    unit (ldg32)."""
+    if mech == "ldg4":
+        return passes * (nbytes // 4)
+    if mech == "ldg32":
+        return passes * ((nbytes + 31) // 32)
+    return passes * (nbytes // 16)
 
 
 def _key(cell: dict, order: str) -> str:
@@ -225,7 +239,8 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                     gbs_max=round(max(gbs), 2) if gbs else None,
                     gbs=[round(v, 2) for v in gbs],
                     window_gbs_median=round(statistics.median(wgbs), 2) if wgbs else None,
-                    issued_ok=all(r.issued_loads == vol // (4 if row["mech"] == "ldg4" else 16) for r in ok),
+                    issued_ok=all(r.issued_loads == _expected_loads(row["mech"], nbytes, row.get("passes", 1))
+                                  for r in ok),
                     checksum_ok=(cks == {ref}),
                     above_datasheet=bool(gbs and max(gbs) > DATASHEET_GBS),
                     frac_of_datasheet=round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,

@@ -14,9 +14,9 @@ from __future__ import annotations
 import statistics
 from dataclasses import dataclass, field
 
-from . import (SL_ASC, SL_CPASYNC, SL_LDG, SL_OK, SL_TMA, SL_U32, SLError, config, sl_plan, sl_sweep)
+from . import (SL_ASC, SL_CPASYNC, SL_LDG, SL_LDG32, SL_OK, SL_TMA, SL_U32, SLError, config, sl_plan, sl_sweep)
 
-MECH_NAMES = {SL_LDG: "ldg", SL_CPASYNC: "cpasync", SL_TMA: "tma"}
+MECH_NAMES = {SL_LDG: "ldg", SL_CPASYNC: "cpasync", SL_TMA: "tma", SL_LDG32: "ldg32"}
 
 
 @dataclass
@@ -52,13 +52,23 @@ class Point:
         """Offered in-flight bytes per CTA (for tie-breaking)."""
         if self.mech == SL_TMA:
             return self.stage_bytes * self.stages
-        return self.k * self.cta * 16
+        return self.k * self.cta * (32 if self.mech == SL_LDG32 else 16)
 
     def label(self) -> str:
         if self.mech == SL_TMA:
             return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}"
         dyn = " dyn" if self.order == 2 else ""
-        return f"{MECH_NAMES[self.mech]} {'K' if self.mech == SL_LDG else 'D'}={self.k} cta={self.cta} cop={self.cop}{dyn}"
+        kd = "D" if self.mech == SL_CPASYNC else "K"
+        return f"{MECH_NAMES[self.mech]} {kd}={self.k} cta={self.cta} cop={self.cop}{dyn}"
+
+    def spec(self) -> str:
+        """The point in parse_point's notation."""
+        if self.mech == SL_TMA:
+            return f"tma:{self.stage_bytes}:{self.stages}:{self.cta}"
+        name = MECH_NAMES[self.mech] + ("dyn" if self.order == 2 else "")
+        if self.mech == SL_LDG and self.order != 2:
+            return f"ldg:{self.k}:{self.cta}:{self.cop}"
+        return f"{name}:{self.k}:{self.cta}"
 
     def as_dict(self) -> dict:
         d = {"mech": MECH_NAMES[self.mech], "cta": self.cta, "grid": self.grid_used, "status": self.status,
@@ -72,10 +82,12 @@ class Point:
 
 
 def parse_point(text: str) -> Point:
-    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'cpasync:D:cta' or 'tma:stage_bytes:stages:cta'."""
+    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta' or
+    'tma:stage_bytes:stages:cta'."""
     f = text.split(":")
-    if f[0] == "ldgdyn":
-        return Point(SL_LDG, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256, order=2)
+    if f[0] in ("ldgdyn", "ldg32dyn", "ldg32"):
+        return Point(SL_LDG32 if f[0].startswith("ldg32") else SL_LDG, k=int(f[1]),
+                     cta=int(f[2]) if len(f) > 2 else 256, order=2 if f[0].endswith("dyn") else 0)
     mech = f[0]
     if mech == "tma":
         return Point(SL_TMA, stage_bytes=int(f[1]), stages=int(f[2]), cta=int(f[3]) if len(f) > 3 else 256)
@@ -90,6 +102,8 @@ def default_points(cta: int = 256) -> list[Point]:
     pts += [Point(SL_LDG, k=k, cta=cta, cop=1) for k in (1, 2, 4, 8)]
     pts += [Point(SL_LDG, k=k, cta=cta, order=2) for k in (2, 3, 4, 6, 8, 12, 16)]
     pts += [Point(SL_LDG, k=k, cta=512, order=2) for k in (2, 4)]
+    pts += [Point(SL_LDG32, k=k, cta=cta) for k in (1, 2, 4)]
+    pts += [Point(SL_LDG32, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in (1, 2, 4, 8)]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n)
             for s in (4096, 16384, 65536) for n in (2, 4, 8) if s * n <= 227 * 1024]

@@ -77,6 +77,18 @@ def test_ldg_dynamic_float(sl, payloads, dt, k):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("k", [1, 3, 8])
+@pytest.mark.parametrize("order", ["asc", "dyn"])
+def test_ldg32_float(sl, payloads, dt, k, order):
+    dev, host, ref, absum, ck, n = payloads[dt]
+    r = sl.sl_run(dev, dtype=dt, cfg=sl.config("ldg32", k=k, cta=256, order=order))
+    assert (r.sum_u32, r.xor_u64) == ck
+    assert r.issued_loads == (NBYTES + 31) // 32
+    ok, rel = _gate(r.fsum, ref, absum, n)
+    assert ok, (r.fsum, ref, rel)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("g", [1, 5, 12])
 def test_ldsts_float(sl, payloads, dt, g):
     _check(sl, payloads[dt], dt, sl.config("ldsts", k=g, cta=256))

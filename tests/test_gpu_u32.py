@@ -163,6 +163,52 @@ def test_ldg4_rejects_other_forms(sl, data):
         assert e.value.status == code, kw
 
 
+def _ldg32_loads(nbytes, passes=1):
+    return passes * ((nbytes + 31) // 32)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("cta", [128, 256, 512])
+@pytest.mark.parametrize("order", ["asc", "desc", "dyn"])
+def test_ldg32_every_shape(sl, data, k, cta, order):
+    """32-byte loads (ld.global.v8): the same checksum at every K, CTA size
+    and traversal; the buffer ends in a half unit (an odd number of 16-byte
+    vectors), which one thread reads with a 16-byte load."""
+    dev, _, want = data
+    assert (NBYTES // 16) % 2 == 1
+    for _ in range(2 if order == "dyn" else 1):
+        r = sl.sl_run(dev, nbytes=NBYTES, dtype=sl.SL_U32, cfg=sl.config("ldg32", k=k, cta=cta, order=order))
+        assert (r.sum_u32, r.xor_u64) == want
+        assert r.issued_loads == _ldg32_loads(NBYTES)
+
+
+@pytest.mark.parametrize("nvec", [0, 1, 2, 3, 31, 33, 255, 257, 4096 + 5, 65536 * 3 + 1])
+@pytest.mark.parametrize("k", [1, 8])
+@pytest.mark.parametrize("order", ["asc", "dyn"])
+def test_ldg32_small_ragged_and_passes(sl, data, nvec, k, order):
+    dev, host, _ = data
+    nbytes = 16 * nvec
+    s, x = oracle.checksum(host[: nbytes // 4])
+    for passes in (1, 3):
+        r = sl.sl_run(dev, nbytes=nbytes, dtype=sl.SL_U32,
+                      cfg=sl.config("ldg32", k=k, cta=128, grid=7, passes=passes, order=order))
+        assert (r.sum_u32, r.xor_u64) == ((passes * s) % (1 << 32), x if passes % 2 else 0)
+        assert r.issued_loads == _ldg32_loads(nbytes, passes)
+
+
+def test_ldg32_needs_32_byte_alignment(sl, data):
+    dev, host, _ = data
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_run(dev.data_ptr() + 16, nbytes=4096, dtype=sl.SL_U32, cfg=sl.config("ldg32", k=2))
+    assert e.value.status == sl.SL_ERR_ALIGN
+    r = sl.sl_run(dev.data_ptr() + 32, nbytes=4096 + 16, dtype=sl.SL_U32, cfg=sl.config("ldg32", k=2))
+    assert (r.sum_u32, r.xor_u64) == oracle.checksum(host[8: 8 + (4096 + 16) // 4])
+    for kw in (dict(k=5), dict(k=16), dict(k=2, cta=1024), dict(k=2, cop=1)):
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_run(dev, nbytes=4096, dtype=sl.SL_U32, cfg=sl.config("ldg32", **kw))
+        assert e.value.status == sl.SL_ERR_ARG, kw
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 8, 12, 16])
 @pytest.mark.parametrize("cta", [128, 256, 512])
 def test_ldg_dynamic_chunks(sl, data, k, cta):
