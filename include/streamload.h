@@ -200,9 +200,9 @@ int sl_flush_l2(void* stream);
  * infeasible cells. */
 int sl_plan(uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out);
 
-/* One streaming pass set over dev_buf[0, bytes) (spec call
+/* One streaming pass set over dev_buf[0, bytes): the call
  * sl_run(buf, bytes, dtype, mech, K or D, cta, grid, order) -> checksum,
- * device ns, issued-load count).  Tiles: LDG and CPASYNC walk tiles of
+ * device ns, issued-load count.  Tiles: LDG and CPASYNC walk tiles of
  * cta*K (or cta*D) 16-byte vectors, CTA b taking tiles b, b+grid, ...
  * (paper §3: each warp's access is contiguous and fully coalesced at every
  * K); load k of thread t reads vector tile*cta*K + k*cta + t; the last tile is
@@ -330,7 +330,7 @@ typedef struct sl_tune_entry {
 
 typedef struct sl_batch sl_batch;  /* opaque */
 
-/* Build a batched streaming checksum over n buffers (spec form 2: a
+/* Build a batched streaming checksum over n buffers (the batched form: a
  * persistent kernel per size class streaming many uneven buffers, in one
  * CUDA-graph launch; no paper counterpart).  Each buffer goes to the first
  * table entry that matches it (SL_ERR_ARG if none).  Buffers are cut into

@@ -37,6 +37,9 @@ GPU and checked against the first cell's checksum):
   ncu  a small case for counter captures (1 GiB, one launch per cell, no
        warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), LDG K=4 and K=12
        with the dynamic-chunk traversal, cp.async D=2, TMA 16 KiB x 2 stages.
+  c2w  the residency grid of c2 at the other two load widths: 4-byte loads
+       (K in {1,2,4,8,16}) and 32-byte loads (K in {1,2,3,4,6,8}); with c2
+       it gives the paper's regime map over warps x width.
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
@@ -81,6 +84,13 @@ def _cells(config: str, sms: int):
             for r in range(1, 9):
                 for k in (1, 2, 3, 4, 6, 8, 12, 16):
                     yield dict(mech="ldg", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
+    elif config == "c2w":
+        for cta in (128, 256, 512):
+            for r in range(1, 9):
+                for k in (1, 2, 4, 8, 16):
+                    yield dict(mech="ldg4", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
+                for k in (1, 2, 3, 4, 6, 8):
+                    yield dict(mech="ldg32", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
     elif config == "c3":
         for k in range(1, 17):
             yield dict(mech="ldg", k=k, cta=256, grid=0, gib=4)
@@ -397,14 +407,19 @@ def regime(values, frac: float = 0.95, tail: int = 3) -> str:
     return "rising-censored"
 
 
+WIDTH_BYTES = {"ldg": 16, "ldg4": 4, "ldg32": 32}
+
+
 def regime_map(rows):
-    """Regime of every LDG K curve of the residency grid (config c2): one
-    curve per (CTA, resident CTAs per SM, order) over the K values present."""
+    """Regime of every plain-load K curve of the residency grid (configs c2
+    and c2w): one curve per (load width in bytes, CTA, resident CTAs per SM,
+    order) over the K values present."""
     curves = {}
     for r in rows:
-        if r.get("config") != "c2" or r.get("status") or r.get("gbs_median") is None:
+        if r.get("config") not in ("c2", "c2w") or r.get("status") or r.get("gbs_median") is None:
             continue
-        curves.setdefault((r["cta"], r["resident_req"], r["order"]), {})[r["k"]] = r["gbs_median"]
+        key = (WIDTH_BYTES[r.get("mech", "ldg")], r["cta"], r["resident_req"], r["order"])
+        curves.setdefault(key, {})[r["k"]] = r["gbs_median"]
     out = {}
     for key, byk in sorted(curves.items()):
         ks = sorted(byk)
@@ -445,7 +460,7 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
+                    choices=["c1", "c2", "c2w", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
                              "cpratio", "ladder", "k1gate", "two"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
@@ -467,7 +482,7 @@ def main(argv=None):
         print(json.dumps({"summary": s}), flush=True)
     for s in cp_ratio(rows):
         print(json.dumps({"cp_ratio": s}), flush=True)
-    if a.config == "c2":
+    if a.config in ("c2", "c2w"):
         rm = regime_map(rows)
         counts = {c: sum(1 for v in rm.values() if v == c) for c in ("saturating", "peak-decline", "rising-censored")}
         print(json.dumps({"regime_counts": counts, "curves": len(rm)}), flush=True)

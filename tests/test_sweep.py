@@ -82,4 +82,9 @@ def test_regime_rule():
 def test_regime_map_groups_curves():
     rows = [{"config": "c2", "status": 0, "cta": 256, "resident_req": 4, "order": "asc", "k": k, "gbs_median": v}
             for k, v in zip((1, 2, 3, 4, 6, 8), (10, 20, 30, 40, 39.5, 39))]
-    assert sweep.regime_map(rows) == {(256, 4, "asc"): "saturating"}
+    assert sweep.regime_map(rows) == {(16, 256, 4, "asc"): "saturating"}
+    wide = [dict(r, config="c2w", mech="ldg32") for r in rows]
+    falling = [dict(r, config="c2w", mech="ldg4", gbs_median=100 - r["k"]) for r in rows]
+    assert sweep.regime_map(rows + wide + falling) == {(16, 256, 4, "asc"): "saturating",
+                                                        (32, 256, 4, "asc"): "saturating",
+                                                        (4, 256, 4, "asc"): "peak-decline"}
