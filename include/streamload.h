@@ -126,6 +126,16 @@ typedef struct sl_config {
                             host buffer directly over the CPU-GPU link (pinned
                             memory, or pageable memory where the device can
                             address it), with no staging copies */
+    uint64_t target_loads; /* 0 (default): exact fixed work, every vector read
+                            once per pass.  > 0: the paper's fixed-iteration
+                            control (§3 "Fixed-work control"): every thread runs
+                            iters = floor(target_loads / (grid*cta*K)) iterations
+                            of K 16-byte loads, wrapping around the buffer
+                            (global tile g covers vectors g*cta*K .. (g+1)*cta*K-1
+                            mod bytes/16), so issued_loads = iters*grid*cta*K.
+                            SL_LDG with SL_ASC / SL_DESC, uint32 payloads, cta
+                            256/512/1024, passes <= 1, buffer of at least one
+                            tile (SL_ERR_ARG otherwise). */
     void*   stream;      /* cudaStream_t to launch on; NULL = legacy default stream */
 } sl_config;
 

@@ -61,6 +61,9 @@ def _load():
             lib.oracle_checksum.restype = None
             lib.oracle_checksum.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                             u32p, ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_wrapped_checksum.restype = None
+            lib.oracle_wrapped_checksum.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                                    u32p, ctypes.POINTER(ctypes.c_uint64)]
             lib.oracle_issued_loads.restype = ctypes.c_uint64
             lib.oracle_issued_loads.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             lib.oracle_fixed_iteration.restype = ctypes.c_double
@@ -99,6 +102,19 @@ def checksum(buf, passes: int = 1) -> tuple[int, int]:
     s = ctypes.c_uint32()
     x = ctypes.c_uint64()
     lib.oracle_checksum(w.ctypes.data, w.size, passes, ctypes.byref(s), ctypes.byref(x))
+    return int(s.value), int(x.value)
+
+
+def wrapped_checksum(buf, nloads: int) -> tuple[int, int]:
+    """(sum_u32, xor_u64) of ``nloads`` 16-byte loads j = 0, 1, ... reading
+    vector j mod (vectors in the buffer): the paper's fixed-iteration reads,
+    which wrap around the allocation (§3 Fixed-work control)."""
+    w = _words(buf)
+    if w.size % 4:
+        raise ValueError("buffer must be a whole number of 16-byte vectors")
+    s = ctypes.c_uint32()
+    x = ctypes.c_uint64()
+    _load().oracle_wrapped_checksum(w.ctypes.data, w.size, int(nloads), ctypes.byref(s), ctypes.byref(x))
     return int(s.value), int(x.value)
 
 

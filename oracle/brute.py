@@ -27,6 +27,21 @@ def checksum(data: bytes, passes: int = 1) -> tuple[int, int]:
     return s, x
 
 
+def wrapped_checksum(data: bytes, nloads: int) -> tuple[int, int]:
+    """Checksum of nloads 16-byte loads where load j reads vector j mod
+    (number of 16-byte vectors): the sink of every loaded vector, in order."""
+    if len(data) % 16:
+        raise ValueError("length must be a multiple of 16")
+    vecs = [data[16 * i:16 * i + 16] for i in range(len(data) // 16)]
+    s = 0
+    x = 0
+    for j in range(nloads if vecs else 0):
+        a, b, c, d = struct.unpack("<4I", vecs[j % len(vecs)])
+        s = (s + a + b + c + d) % (1 << 32)
+        x ^= (a | (b << 32)) ^ (c | (d << 32))
+    return s, x
+
+
 def _fp8_e4m3(b: int) -> float:
     sign = -1.0 if b & 0x80 else 1.0
     e = (b >> 3) & 0xF

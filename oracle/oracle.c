@@ -78,6 +78,31 @@ void oracle_checksum(const uint32_t *w, uint64_t nwords, uint64_t passes,
     *xor_out = x;
 }
 
+/* The checksum of the paper's fixed-iteration reads (§3 "Fixed-work
+ * control", with the allocation sweep's wrap-around): nloads 16-byte loads
+ * j = 0, 1, ..., nloads-1, load j reading 16-byte vector (j mod nvec) of a
+ * buffer of nvec = nwords/4 vectors.  Folded literally, one load at a time.
+ * nwords must be a multiple of 4; nvec == 0 gives (0, 0). */
+void oracle_wrapped_checksum(const uint32_t *w, uint64_t nwords, uint64_t nloads,
+                             uint32_t *sum_out, uint64_t *xor_out)
+{
+    uint64_t nvec = nwords / 4;
+    uint32_t s = 0;
+    uint64_t x = 0;
+    uint64_t v = 0; /* j mod nvec */
+    if (nvec == 0)
+        nloads = 0;
+    for (uint64_t j = 0; j < nloads; ++j) {
+        const uint32_t *q = w + 4 * v;
+        s += q[0] + q[1] + q[2] + q[3];
+        x ^= ((uint64_t)q[0] | ((uint64_t)q[1] << 32)) ^ ((uint64_t)q[2] | ((uint64_t)q[3] << 32));
+        if (++v == nvec)
+            v = 0;
+    }
+    *sum_out = s;
+    *xor_out = x;
+}
+
 /* ---- issued-load accounting ------------------------------------------- */
 
 /* The build's fixed-work control: one 16-byte logical load per 16 bytes per

@@ -80,7 +80,7 @@ def _stream_handle(stream):
 
 def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *, stage_bytes: int = 16384,
            stages: int = 4, flush_l2: bool = False, passes: int = 1, cop: int = SL_COP_CG,
-           debug_flags: int = 0, host_direct: bool = False, stream=None) -> sl_config:
+           debug_flags: int = 0, host_direct: bool = False, target_loads: int = 0, stream=None) -> sl_config:
     """Build an sl_config.  mech: "ldg" / "cpasync" / "tma" (or the enum);
     k: K for LDG, depth D for cp.async; stage_bytes/stages for TMA."""
     c = sl_config()
@@ -96,6 +96,7 @@ def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *
     c.cop = int(cop)
     c.debug_flags = int(debug_flags)
     c.host_direct = int(bool(host_direct))
+    c.target_loads = int(target_loads)
     c.stream = _stream_handle(stream)
     return c
 

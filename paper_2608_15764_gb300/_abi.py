@@ -47,6 +47,7 @@ class sl_config(ctypes.Structure):
         ("cop", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
         ("host_direct", ctypes.c_int32),
+        ("target_loads", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -123,8 +124,8 @@ class sl_tune_entry(ctypes.Structure):
 
 
 assert ctypes.sizeof(sl_batch_desc) == 24
-assert ctypes.sizeof(sl_tune_entry) == 80
-assert ctypes.sizeof(sl_config) == 56
+assert ctypes.sizeof(sl_tune_entry) == 88
+assert ctypes.sizeof(sl_config) == 64
 assert ctypes.sizeof(sl_result) == 72
 RESULT_BYTES = ctypes.sizeof(sl_result)
 

@@ -217,6 +217,8 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (cfg->order != SL_ASC && cfg->order != SL_DESC && cfg->order != SL_DYN)
         return fail(SL_ERR_ARG, "bad order %d", cfg->order);
     const bool dyn = cfg->order == SL_DYN;
+    const bool fixed = cfg->target_loads > 0;
+    if (fixed && cfg->mech != SL_LDG) return fail(SL_ERR_ARG, "the fixed-iteration control is implemented for SL_LDG");
     if (dyn && ((cfg->mech != SL_LDG && cfg->mech != SL_LDG32) || cfg->cop != SL_COP_CG))
         return fail(SL_ERR_ARG, "the SL_DYN traversal is implemented for SL_LDG / SL_LDG32 with SL_COP_CG");
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
@@ -229,6 +231,23 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     case SL_LDG:
         if (cfg->k < 1 || cfg->k > SL_MAX_K) return fail(SL_ERR_ARG, "LDG K %d not in 1..%d", cfg->k, SL_MAX_K);
         if (cfg->cop < SL_COP_CG || cfg->cop > SL_COP_NC_NA_L2_256) return fail(SL_ERR_ARG, "bad cop %d", cfg->cop);
+        if (fixed) {
+            if (dyn || cfg->cop != SL_COP_CG || dtype != SL_U32 || cfg->passes > 1)
+                return fail(SL_ERR_ARG, "the fixed-iteration control takes SL_ASC / SL_DESC, SL_COP_CG, uint32 "
+                            "payloads and passes <= 1");
+            p->fn = sl::ldg_fixed_kernel(dtype, cfg->k, cta);
+            if (!p->fn)
+                return fail(SL_ERR_ARG, "no fixed-iteration LDG kernel for K %d, cta %d (K in {1,2,3,4,6,8,12,16}, "
+                            "cta 256/512/1024)", cfg->k, cta);
+            if (bytes / 16 < static_cast<uint64_t>(cta) * cfg->k)
+                return fail(SL_ERR_ARG, "the fixed-iteration control needs a buffer of at least one tile "
+                            "(%d x %d vectors)", cta, cfg->k);
+            p->block = cta;
+            p->smem = 0;
+            tile_vec = static_cast<uint64_t>(cta) * cfg->k;
+            p->warps = cta / 32;
+            break;
+        }
         p->fn = dyn ? sl::ldg_dyn_kernel(dtype, cfg->k, cta) : sl::ldg_kernel(dtype, cfg->k, cta, cfg->cop);
         if (!p->fn && dyn)
             return fail(SL_ERR_ARG, "no SL_DYN LDG kernel for K %d, cta %d (K in {1,2,3,4,6,8,12,16}, "
@@ -307,7 +326,9 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     // K in-flight 16-byte loads need 4K registers.  Where the CTA size caps
     // registers below that (CTA 1024 with large K), the compiler interleaves
     // loads with folds and K would no longer be the offered ILP.
-    if ((cfg->mech == SL_LDG || cfg->mech == SL_LDSTS) && fi->regs < 4 * cfg->k + 16)
+    // (the fixed-iteration kernel keeps fewer values live besides the loaded
+    // vectors: its floor is K vectors + pointer, tile start and checksum)
+    if ((cfg->mech == SL_LDG || cfg->mech == SL_LDSTS) && fi->regs < 4 * cfg->k + (fixed ? 8 : 16))
         return fail(SL_ERR_INFEASIBLE, "%d registers per thread cannot hold K=%d loads in flight at cta %d",
                     fi->regs, cfg->k, cta);
     if (cfg->mech == SL_LDG32 && fi->regs < 8 * cfg->k + 16)
@@ -327,11 +348,14 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     // (SL_LDG32: 32-byte units, a final half unit included)
     const uint64_t nvec = bytes / (cfg->mech == SL_LDG4 ? 4 : 16);
     const uint64_t units = cfg->mech == SL_LDG32 ? (nvec + 1) / 2 : nvec;
-    const uint64_t ntiles = (units + tile_vec - 1) / tile_vec;
     int64_t grid = cfg->grid;
     if (grid <= 0) grid = static_cast<int64_t>(std::min(4, p->resident)) * c->info.sm_count;
     if (grid > MAX_GRID) return fail(SL_ERR_ARG, "grid %lld > %lld", (long long)grid, (long long)MAX_GRID);
-    p->grid = nvec == 0 ? 0 : grid;
+    // fixed-iteration control: iters tiles per CTA, all grid*iters tiles wrap
+    // around the buffer; otherwise the tiles that cover the buffer once
+    const uint64_t fixed_iters = fixed ? cfg->target_loads / (static_cast<uint64_t>(grid) * tile_vec) : 0;
+    const uint64_t ntiles = fixed ? fixed_iters * static_cast<uint64_t>(grid) : (units + tile_vec - 1) / tile_vec;
+    p->grid = (nvec == 0 || (fixed && fixed_iters == 0)) ? 0 : grid;
     // The kernels count tiles and per-thread loads in 32 bits.
     const uint64_t total = ntiles * passes;
     const uint64_t per_thread = ((total + grid - 1) / grid) * ((tile_vec + cta - 1) / cta);
@@ -636,6 +660,7 @@ int sl_twostream(const void* buf_a, uint64_t bytes_a, const void* buf_b, uint64_
 
 int sl_run_host(const void* host_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
     if (!out || !cfg) return fail(SL_ERR_ARG, "NULL argument");
+    if (cfg->target_loads) return fail(SL_ERR_ARG, "sl_run_host runs exact fixed work only (target_loads 0)");
     if (bytes > 0 && !host_buf) return fail(SL_ERR_ARG, "host buffer is NULL");
     if ((bytes & 15u) != 0) return fail(SL_ERR_ALIGN, "bytes not a multiple of 16");
     DevCtx* c = nullptr;

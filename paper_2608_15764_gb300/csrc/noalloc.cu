@@ -66,6 +66,7 @@ extern "C" int sl_run_noalloc(const void* dev_buf, uint64_t bytes, int32_t dtype
     if (cfg->mech != SL_LDG) return na_fail(SL_ERR_ARG, "sl_run_noalloc supports the LDG mechanism only");
     if (cfg->flush_l2) return na_fail(SL_ERR_ARG, "sl_run_noalloc cannot flush L2 (the flush buffer is allocated)");
     if (cfg->debug_flags) return na_fail(SL_ERR_ARG, "sl_run_noalloc takes no debug flags");
+    if (cfg->target_loads) return na_fail(SL_ERR_ARG, "sl_run_noalloc runs exact fixed work only (target_loads 0)");
     if (dtype < SL_U32 || dtype > SL_FP8_E4M3) return na_fail(SL_ERR_ARG, "bad dtype");
     if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u)) return na_fail(SL_ERR_ARG, "dev_out NULL or not 8-byte aligned");
     if ((bytes & 15u) != 0) return na_fail(SL_ERR_ALIGN, "bytes not a multiple of 16");

@@ -58,6 +58,7 @@ const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
 const void* ldg4_kernel(int dtype, int k, int cta);
 const void* ldg32_kernel(int dtype, int k, int cta, bool dyn);
+const void* ldg_fixed_kernel(int dtype, int k, int cta);
 
 // Two co-resident streams in one CTA (k_two.cu).  Stream A = warps
 // [0, warps_a), stream B = the warps_b warps after them; one CTA per SM.

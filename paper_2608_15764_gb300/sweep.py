@@ -40,6 +40,11 @@ GPU and checked against the first cell's checksum):
   c2w  the residency grid of c2 at the other two load widths: 4-byte loads
        (K in {1,2,4,8,16}) and 32-byte loads (K in {1,2,3,4,6,8}); with c2
        it gives the paper's regime map over warps x width.
+  fixedit  the paper's own fixed-iteration control (§3, §4.2): the primary
+       cell shape (1,024-thread CTAs, .cg, 16 B) issuing 16,785 MiB of loads
+       that wrap around a 512 MiB or 4 GiB allocation, at 132 CTAs (the
+       paper's H100) and one CTA per GB300 SM, K in {1,2,4,8}; reports the
+       issued counts (mismatch across K) and GB/s of the issued bytes.
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
@@ -84,6 +89,15 @@ def _cells(config: str, sms: int):
             for r in range(1, 9):
                 for k in (1, 2, 3, 4, 6, 8, 12, 16):
                     yield dict(mech="ldg", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
+    elif config == "fixedit":
+        # paper §3 / §4.2: the primary cell under the paper's own fixed-iteration
+        # control (16,785 MiB of 16-byte loads, wrapping over the allocation),
+        # at the paper's 132 CTAs and at GB300's SM count
+        target = 16785 * (1 << 20) // 16
+        for gib in (0.5, 4):
+            for grid in (132, sms):
+                for k in (1, 2, 4, 8):
+                    yield dict(mech="ldg", k=k, cta=1024, grid=grid, target_loads=target, gib=gib)
     elif config == "c2w":
         for cta in (128, 256, 512):
             for r in range(1, 9):
@@ -208,7 +222,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
             cfgs, keep = [], []
             for c in seq:
                 passes = c.get("passes", 1)
-                kw = dict(cta=c["cta"], grid=c["grid"], passes=passes)
+                kw = dict(cta=c["cta"], grid=c["grid"], passes=passes, target_loads=c.get("target_loads", 0))
                 if c["mech"] == "tma":
                     cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
                 else:
@@ -235,11 +249,18 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
             res = sl.sl_sweep(buf, cfgs, dtype=sl.SL_U32, repeats=repeats, warmup=warmup, sweep_order="asc")
             for row, rr in zip(keep, res):
                 ok = [r for r in rr if r.status == 0]
-                vol = nbytes * row.get("passes", 1)  # bytes issued per launch
+                fixed = row.get("target_loads", 0) > 0
+                if fixed:  # the paper's fixed-iteration control: bytes = 16 x loads issued
+                    tk = row["grid"] * row["cta"] * row["k"]
+                    want_loads = row["target_loads"] // tk * tk
+                    vol = 16 * want_loads
+                else:
+                    want_loads = _expected_loads(row["mech"], nbytes, row.get("passes", 1))
+                    vol = nbytes * row.get("passes", 1)  # bytes issued per launch
                 gbs = [vol / r.device_ns for r in ok if r.device_ns]
                 wgbs = [vol / r.window_ns for r in ok if r.window_ns]
                 cks = {(r.sum_u32, r.xor_u64) for r in ok}
-                if ref is None and cks:
+                if ref is None and cks and not fixed:
                     ref = next(iter(cks))
                 row.update(
                     status=0 if len(ok) == len(rr) else rr[0].status,
@@ -249,9 +270,9 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                     gbs_max=round(max(gbs), 2) if gbs else None,
                     gbs=[round(v, 2) for v in gbs],
                     window_gbs_median=round(statistics.median(wgbs), 2) if wgbs else None,
-                    issued_ok=all(r.issued_loads == _expected_loads(row["mech"], nbytes, row.get("passes", 1))
-                                  for r in ok),
-                    checksum_ok=(cks == {ref}),
+                    issued=ok[0].issued_loads if ok else None,
+                    issued_ok=all(r.issued_loads == want_loads for r in ok),
+                    checksum_ok=(len(cks) == 1) if fixed else (cks == {ref}),
                     above_datasheet=bool(gbs and max(gbs) > DATASHEET_GBS),
                     frac_of_datasheet=round(statistics.median(gbs) / DATASHEET_GBS, 4) if gbs else None,
                 )
@@ -441,6 +462,22 @@ def cp_ratio(rows):
             for (w, g, o), d in sorted(by.items()) if "cpasync" in d and "ldsts" in d]
 
 
+def fixed_mismatch(rows):
+    """Paper §4.2 "Exact-work accounting" under the fixed-iteration control:
+    per (allocation, grid, order) the issued loads at each K (from the
+    launches' own counters) and the largest relative mismatch across K."""
+    groups = {}
+    for r in rows:
+        if r.get("target_loads") and not r.get("status") and r.get("issued") is not None:
+            groups.setdefault((r["gib"], r["grid"], r["order"]), {})[r["k"]] = r["issued"]
+    out = []
+    for (gib, grid, order), byk in sorted(groups.items()):
+        hi, lo = max(byk.values()), min(byk.values())
+        out.append({"gib": gib, "grid": grid, "order": order, "issued": {str(k): v for k, v in sorted(byk.items())},
+                    "max_mismatch_pct": round(100.0 * (hi - lo) / hi, 6) if hi else 0.0})
+    return out
+
+
 def summarize(rows):
     """K=2 -> K=8 endpoint change per (config group, order) where both exist."""
     out = []
@@ -460,7 +497,7 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c2w", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
+                    choices=["c1", "c2", "c2w", "fixedit", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
                              "cpratio", "ladder", "k1gate", "two"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
@@ -482,6 +519,9 @@ def main(argv=None):
         print(json.dumps({"summary": s}), flush=True)
     for s in cp_ratio(rows):
         print(json.dumps({"cp_ratio": s}), flush=True)
+    if a.config == "fixedit":
+        for s in fixed_mismatch(rows):
+            print(json.dumps({"fixed_iteration": s}), flush=True)
     if a.config in ("c2", "c2w"):
         rm = regime_map(rows)
         counts = {c: sum(1 for v in rm.values() if v == c) for c in ("saturating", "peak-decline", "rising-censored")}

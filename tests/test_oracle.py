@@ -129,6 +129,24 @@ def test_paper_fixed_work_mismatch(golden_dir):
     assert issued[2] == issued[3] == issued[0] - 2 * threads
 
 
+@pytest.mark.parametrize("nvec,nloads", [(0, 5), (1, 0), (1, 7), (3, 10), (5, 5), (8, 37), (33, 200), (64, 64)])
+def test_wrapped_checksum_brute_force(nvec, nloads):
+    b = _rand_bytes(16 * nvec)
+    assert oracle.wrapped_checksum(b, nloads) == brute.wrapped_checksum(b.tobytes(), nloads)
+
+
+def test_wrapped_checksum_closed_forms():
+    """q whole wraps are q passes; a partial wrap adds the prefix of r vectors;
+    below one wrap it is the checksum of the prefix."""
+    b = _rand_bytes(16 * 1000)
+    w = b.view(np.uint32)
+    for q, r in [(0, 1), (0, 999), (1, 0), (2, 0), (3, 17), (66, 123)]:
+        got = oracle.wrapped_checksum(b, q * 1000 + r)
+        want = oracle.combine([oracle.checksum(w, q) if q else (0, 0), oracle.checksum(w[:4 * r])])
+        assert got == want, (q, r)
+    assert oracle.wrapped_checksum(b, 0) == (0, 0)
+
+
 def test_fixed_iteration_exact_when_divisible():
     issued, mm = oracle.fixed_iteration(1024 * 256 * 16, 1024 * 256, [1, 2, 4, 8, 16])
     assert mm == 0.0 and len(set(issued)) == 1

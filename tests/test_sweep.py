@@ -88,3 +88,17 @@ def test_regime_map_groups_curves():
     assert sweep.regime_map(rows + wide + falling) == {(16, 256, 4, "asc"): "saturating",
                                                         (32, 256, 4, "asc"): "saturating",
                                                         (4, 256, 4, "asc"): "peak-decline"}
+
+
+def test_fixed_mismatch_summary():
+    """The GPU-counter form of the paper's §4.2 mismatch: issued loads per K
+    from the fixed-iteration cells, largest relative spread across K."""
+    threads, target = 132 * 1024, 16785 * (1 << 20) // 16
+    rows = []
+    for k in (1, 2, 4, 8):
+        issued = target // (threads * k) * threads * k
+        rows.append({"config": "fixedit", "target_loads": target, "status": 0, "issued": issued, "gib": 0.5,
+                     "grid": 132, "order": "asc", "k": k})
+    (s,) = sweep.fixed_mismatch(rows)
+    assert s["max_mismatch_pct"] == 0.024576
+    assert s["issued"]["1"] == s["issued"]["2"] == 8138 * threads
