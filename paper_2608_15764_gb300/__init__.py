@@ -146,6 +146,16 @@ def sl_enqueue(buf, dev_out, nbytes=None, dtype=SL_U32, cfg: sl_config | None = 
     _check(load().sl_enqueue(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), _addr(dev_out)))
 
 
+def sl_enqueue_steps(buf, dev_out, steps: int, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> None:
+    """`steps` back-to-back passes on cfg.stream, pass i's result to the i-th
+    RESULT_BYTES slot of the device buffer dev_out; passes after the first
+    are programmatic dependent launches (their start overlaps the previous
+    pass's tail)."""
+    cfg = cfg or config()
+    _check(load().sl_enqueue_steps(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), int(steps),
+                                   _addr(dev_out)))
+
+
 def sl_sweep(buf, cells, nbytes=None, dtype=SL_U32, repeats: int = 1, warmup: int = 1,
              sweep_order=SL_ASC) -> list[list[sl_result]]:
     """Returns rows[cell][repeat] (in cell order whatever the sweep order)."""

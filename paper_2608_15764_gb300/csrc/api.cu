@@ -376,11 +376,27 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     return SL_OK;
 }
 
-int launch(const Plan& p, cudaStream_t s) {
+int launch(const Plan& p, cudaStream_t s, bool programmatic = false) {
     if (p.grid == 0) return SL_OK;
     KArgs a = p.args;
     void* args[] = {&a};
-    CUDA_TRY(cudaLaunchKernel(p.fn, dim3(static_cast<unsigned>(p.grid)), dim3(p.block), args, p.smem, s));
+    if (!programmatic) {
+        CUDA_TRY(cudaLaunchKernel(p.fn, dim3(static_cast<unsigned>(p.grid)), dim3(p.block), args, p.smem, s));
+        return SL_OK;
+    }
+    // programmatic dependent launch: may begin once every CTA of the previous
+    // kernel on the stream has executed griddepcontrol.launch_dependents
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(static_cast<unsigned>(p.grid));
+    lc.blockDim = dim3(p.block);
+    lc.dynamicSmemBytes = p.smem;
+    lc.stream = s;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    CUDA_TRY(cudaLaunchKernelExC(&lc, p.fn, args));
     return SL_OK;
 }
 
@@ -511,6 +527,44 @@ int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_conf
     if (rc) return rc;
     std::lock_guard<std::recursive_mutex> g(c->mu);
     return enqueue_locked(c, dev_buf, bytes, dtype, cfg, dev_out, false, nullptr);
+}
+
+int sl_enqueue_steps(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, int32_t steps,
+                     sl_result* dev_out) {
+    if (!cfg) return fail(SL_ERR_ARG, "cfg is NULL");
+    if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u)) return fail(SL_ERR_ARG, "dev_out NULL or misaligned");
+    if (steps < 1) return fail(SL_ERR_ARG, "steps %d < 1", steps);
+    if (cfg->order != SL_ASC && cfg->order != SL_DESC)
+        return fail(SL_ERR_ARG, "sl_enqueue_steps takes the SL_ASC / SL_DESC traversals only");
+    if (cfg->mech == SL_TMA) return fail(SL_ERR_ARG, "sl_enqueue_steps does not take SL_TMA");
+    if (cfg->flush_l2) return fail(SL_ERR_ARG, "sl_enqueue_steps takes flush_l2 == 0");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    Plan p;
+    rc = make_plan(c, dev_buf, bytes, dtype, cfg, &p);
+    if (rc) return rc;
+    if (p.grid == 0) {  // empty buffer (or no fixed iteration): zero results
+        for (int32_t i = 0; i < steps; ++i) {
+            rc = enqueue_locked(c, dev_buf, bytes, dtype, cfg, dev_out + i, false, nullptr);
+            if (rc) return rc;
+        }
+        return SL_OK;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid));
+    if (rc) return rc;
+    p.args.parts = c->parts;
+    p.args.window = sl::ctrl_window(c->err);
+    p.args.err = sl::ctrl_err(c->err);
+    p.args.done = sl::ctrl_done(c->err);
+    for (int32_t i = 0; i < steps; ++i) {
+        p.args.result = dev_out + i;
+        rc = launch(p, s, i > 0);
+        if (rc) return rc;
+    }
+    return SL_OK;
 }
 
 int sl_sweep(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cells, int32_t ncells,

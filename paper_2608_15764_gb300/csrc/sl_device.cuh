@@ -261,6 +261,13 @@ __device__ __forceinline__ void final_combine(const KArgs& a) {
     }
 }
 
+// This CTA's %globaltimer start, kept in shared memory by cta_start (below)
+// and published by cta_finish.
+__device__ __forceinline__ uint64_t& cta_start_stamp() {
+    __shared__ uint64_t t0;
+    return t0;
+}
+
 // End of a streaming kernel: every folding warp (all 32 lanes present)
 // reduces its accumulators and lane 0 puts the warp partial in shared memory;
 // after a CTA barrier warp 0 merges the warp partials (butterfly, fixed
@@ -273,6 +280,11 @@ __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint3
                                            const KArgs& a) {
     __shared__ WarpPartial sp[32];
     const uint32_t lane = threadIdx.x & 31;
+    // A launch that may have started before the previous one finished
+    // (programmatic dependent launch) touches the shared scratch (partials,
+    // window, CTA counter) only once that launch has completed and its writes
+    // are visible; without a prerequisite grid this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (folds) {
         uint32_t s = acc.s;
         uint64_t x = (static_cast<uint64_t>(acc.xh) << 32) | acc.xl, n = acc.n;
@@ -312,6 +324,7 @@ __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint3
             p.hi = hi;
             p.lo = lo;
             a.parts[blockIdx.x] = p;
+            atomicMin(reinterpret_cast<unsigned long long*>(a.window), cta_start_stamp());
             atomicMax(reinterpret_cast<unsigned long long*>(a.window + 1), gtimer());
         }
     }
@@ -349,10 +362,14 @@ struct TileCursor {
     }
 };
 
-// Start of a streaming kernel: thread 0 lowers the launch's start stamp to
-// this CTA's %globaltimer (no register holds it through the kernel).
-__device__ __forceinline__ void cta_start(const KArgs& a) {
-    if (threadIdx.x == 0) atomicMin(reinterpret_cast<unsigned long long*>(a.window), gtimer());
+// Start of a streaming kernel: thread 0 keeps this CTA's %globaltimer start
+// in shared memory (no register holds it through the kernel), and the CTA
+// lets a programmatically dependent next launch begin (griddepcontrol; a
+// no-op unless the next launch asked for programmatic stream serialization).
+// Nothing here touches the launch's scratch: that waits for cta_finish.
+__device__ __forceinline__ void cta_start(const KArgs&) {
+    if (threadIdx.x == 0) cta_start_stamp() = gtimer();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 }  // namespace sl

@@ -1,0 +1,113 @@
+"""GPU parity of sl_enqueue_steps: back-to-back passes whose launches after
+the first are programmatic dependent launches (a pass may start loading
+while the previous pass's tail runs).  Every pass's result must equal the
+oracle's checksum and a separate launch's result, whatever the mechanism,
+grid or interleaving with ordinary launches."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_15764_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SEED = 1
+NBYTES = (1 << 24) + 16 * 1237
+
+
+@pytest.fixture(scope="module")
+def sl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2608_15764_gb300 as sl
+    sl.load()
+    return sl
+
+
+@pytest.fixture(scope="module")
+def data(sl):
+    dev = torch.empty(NBYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(dev, seed=SEED)
+    host = workloads.splitmix_u32(SEED, NBYTES // 4)
+    return dev, host, oracle.checksum(host)
+
+
+def _results(sl, out, n):
+    raw = out.cpu().numpy().tobytes()
+    rb = sl.RESULT_BYTES
+    return [sl.sl_result.from_buffer_copy(raw[rb * i:rb * (i + 1)]) for i in range(n)]
+
+
+@pytest.mark.parametrize("mech,kw,loads", [
+    ("ldg", dict(k=2, cta=256), 16), ("ldg", dict(k=6, cta=256, order="desc"), 16),
+    ("ldg", dict(k=4, cta=128, grid=10007), 16), ("ldg", dict(k=1, cta=1024, grid=152), 16),
+    ("ldg32", dict(k=4, cta=256), 32), ("ldg4", dict(k=4, cta=256), 4),
+    ("cpasync", dict(k=4, cta=256), 16), ("ldsts", dict(k=4, cta=256), 16),
+])
+def test_steps_each_pass_matches_oracle(sl, data, mech, kw, loads):
+    dev, _, want = data
+    steps = 9
+    out = torch.zeros(steps * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, steps, dtype=sl.SL_U32, cfg=sl.config(mech, **kw))
+    torch.cuda.synchronize()
+    want_loads = (NBYTES + loads - 1) // loads
+    for r in _results(sl, out, steps):
+        assert (r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*want, want_loads, 0)
+        assert r.window_ns > 0
+
+
+def test_steps_interleaved_with_ordinary_launches(sl, data):
+    dev, _, want = data
+    out = torch.zeros(12 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    cfg = sl.config("ldg", k=3, cta=256)
+    sl.sl_enqueue_steps(dev, out[: 4 * sl.RESULT_BYTES], 4, dtype=sl.SL_U32, cfg=cfg)
+    sl.sl_enqueue(dev, out[4 * sl.RESULT_BYTES:], dtype=sl.SL_U32, cfg=sl.config("ldg", k=12, order="dyn"))
+    sl.sl_enqueue_steps(dev, out[5 * sl.RESULT_BYTES:], 6, dtype=sl.SL_U32, cfg=sl.config("ldg32", k=2))
+    r = sl.sl_run(dev, dtype=sl.SL_U32, cfg=cfg)  # ordered after the enqueued work
+    assert (r.sum_u32, r.xor_u64) == want
+    sl.sl_enqueue(dev, out[11 * sl.RESULT_BYTES:], dtype=sl.SL_U32, cfg=cfg)
+    torch.cuda.synchronize()
+    for r in _results(sl, out, 12):
+        assert (r.sum_u32, r.xor_u64, r.status) == (*want, 0)
+
+
+def test_steps_float_sums_equal_a_single_launch(sl):
+    """Same launch shape, same partial order: the float sum of every pass is
+    bit-identical to sl_run's."""
+    x = workloads.payload(workloads.F32, (1 << 22) + 5 * 4)
+    dev = torch.from_numpy(x.view(np.uint8)).cuda()
+    cfg = sl.config("ldg", k=4, cta=256)
+    ref = sl.sl_run(dev, dtype=sl.SL_F32, cfg=cfg)
+    out = torch.zeros(5 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, 5, dtype=sl.SL_F32, cfg=cfg)
+    torch.cuda.synchronize()
+    for r in _results(sl, out, 5):
+        assert (r.fsum, r.sum_u32, r.xor_u64) == (ref.fsum, ref.sum_u32, ref.xor_u64)
+
+
+def test_steps_fixed_iteration(sl, data):
+    dev, host, _ = data
+    target = 2 * (NBYTES // 16) + 999
+    cfg = sl.config("ldg", k=4, cta=256, grid=608, target_loads=target)
+    out = torch.zeros(4 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, 4, dtype=sl.SL_U32, cfg=cfg)
+    torch.cuda.synchronize()
+    issued, _ = oracle.fixed_iteration(target, 608 * 256, [4])
+    want = oracle.wrapped_checksum(host, issued[0])
+    for r in _results(sl, out, 4):
+        assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, issued[0])
+
+
+def test_steps_empty_and_rejected(sl, data):
+    dev, _, _ = data
+    out = torch.ones(3 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, 3, nbytes=0, dtype=sl.SL_U32, cfg=sl.config("ldg"))
+    torch.cuda.synchronize()
+    for r in _results(sl, out, 3):
+        assert (r.sum_u32, r.xor_u64, r.issued_loads) == (0, 0, 0)
+    for cfg, steps in [(sl.config("ldg", order="dyn"), 2), (sl.config("tma"), 2),
+                       (sl.config("ldg", flush_l2=True), 2), (sl.config("ldg"), 0)]:
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_enqueue_steps(dev, out, steps, dtype=sl.SL_U32, cfg=cfg)
+        assert e.value.status == sl.SL_ERR_ARG
