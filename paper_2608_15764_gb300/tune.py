@@ -30,6 +30,7 @@ class Point:
     cop: int = 0
     order: int = 0        # SL_ASC, or SL_DYN (dynamic contiguous chunks, LDG)
     gbs: list = field(default_factory=list)  # per repeat
+    step_gbs: list = field(default_factory=list)  # back-to-back passes, per repeat
     window_gbs: list = field(default_factory=list)
     status: int = SL_OK
     resident: int = 0
@@ -46,6 +47,16 @@ class Point:
     @property
     def median(self) -> float:
         return statistics.median(self.gbs) if self.gbs else 0.0
+
+    @property
+    def step_median(self) -> float:
+        return statistics.median(self.step_gbs) if self.step_gbs else 0.0
+
+    @property
+    def overlapped(self) -> bool:
+        """Back-to-back passes run as programmatic dependent launches
+        (sl_enqueue_steps): grid-stride traversals of every mechanism but TMA."""
+        return self.mech != SL_TMA and self.order != 2
 
     @property
     def offered(self) -> int:
@@ -74,6 +85,8 @@ class Point:
         d = {"mech": MECH_NAMES[self.mech], "cta": self.cta, "grid": self.grid_used, "status": self.status,
              "resident_per_sm": self.resident, "gbs_median": round(self.median, 1),
              "gbs": [round(v, 1) for v in self.gbs]}
+        if self.step_gbs:
+            d.update(steps_gbs_median=round(self.step_median, 1), steps_overlapped=self.overlapped)
         if self.mech == SL_TMA:
             d.update(stage_bytes=self.stage_bytes, stages=self.stages)
         else:
@@ -133,10 +146,50 @@ def measure(buf, nbytes: int, points: list[Point], dtype: int = SL_U32, repeats:
     return points
 
 
-def choose(points: list[Point], tie_frac: float = 0.005) -> Point:
-    ok = [p for p in points if p.status == SL_OK and p.gbs]
+def measure_steps(buf, nbytes: int, points: list[Point], steps: int = 8, repeats: int = 3,
+                  dtype: int = SL_U32) -> list[Point]:
+    """Throughput of `steps` back-to-back passes for every measured point:
+    one sl_enqueue_steps call (overlapped passes) where the point allows it,
+    else `steps` sl_enqueue calls; CUDA events on the current stream around
+    the passes, after one untimed round; median of `repeats` into step_gbs."""
+    import torch
+
+    from . import RESULT_BYTES, sl_enqueue, sl_enqueue_steps
+    out = torch.zeros(steps * RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(p, cfg):
+        if p.overlapped:
+            sl_enqueue_steps(buf, out, steps, nbytes=nbytes, dtype=dtype, cfg=cfg)
+        else:
+            for i in range(steps):
+                sl_enqueue(buf, out[i * RESULT_BYTES:], nbytes=nbytes, dtype=dtype, cfg=cfg)
+
+    for p in points:
+        if p.status != SL_OK or not p.gbs:
+            continue
+        cfg = p.cfg()
+        run(p, cfg)
+        p.step_gbs = []
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run(p, cfg)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            p.step_gbs.append(nbytes * steps / (e0.elapsed_time(e1) * 1e6))
+    return points
+
+
+def choose(points: list[Point], tie_frac: float = 0.005, steps: bool = False) -> Point:
+    """Highest median GB/s of single launches (steps=False) or of back-to-back
+    passes (steps=True); ties within tie_frac go to fewer bytes in flight,
+    then LDG before cp.async before TMA."""
+    def val(p):
+        return p.step_median if steps else p.median
+    ok = [p for p in points if p.status == SL_OK and (p.step_gbs if steps else p.gbs)]
     if not ok:
         raise RuntimeError("no feasible measured point")
-    best = max(p.median for p in ok)
-    ties = [p for p in ok if p.median >= best * (1 - tie_frac)]
+    best = max(val(p) for p in ok)
+    ties = [p for p in ok if val(p) >= best * (1 - tie_frac)]
     return min(ties, key=lambda p: (p.offered, p.mech))
