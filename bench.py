@@ -260,6 +260,11 @@ def run_ours(a):
     nbytes = int(a.gib * (1 << 30)) // 16 * 16
     buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     sl.sl_fill_splitmix64(buf, seed=1)
+    # a second resident copy: back-to-back passes alternate between the two,
+    # so no pass can find the previous pass's lines in L2
+    buf2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(buf2, seed=1)
+    bufs = [buf, buf2]
     torch.cuda.synchronize()
 
     # ---- K-response curves and the choice (rank 0 decides, all ranks follow)
@@ -270,11 +275,11 @@ def run_ours(a):
     # back-to-back passes of every point, which picks the timed configuration
     if rank == 0 and a.choice:
         tune.measure(buf, nbytes, points, repeats=1, warmup=1)
-        tune.measure_steps(buf, nbytes, points, steps=8, repeats=1)
+        tune.measure_steps(bufs, nbytes, points, steps=8, repeats=1)
         choice = [0]
     elif rank == 0:
         tune.measure(buf, nbytes, points, repeats=a.curve_repeats, warmup=1)
-        tune.measure_steps(buf, nbytes, points, steps=8, repeats=a.curve_repeats)
+        tune.measure_steps(bufs, nbytes, points, steps=8, repeats=a.curve_repeats)
         best = tune.choose(points, steps=True)
         choice = [points.index(best)]
     else:
@@ -290,10 +295,11 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
     rb = sl.RESULT_BYTES
     if best.overlapped:
-        sl.sl_enqueue_steps(buf, dev_out, a.warmup, dtype=sl.SL_U32, cfg=cfg)
+        cfg = best.cfg(grid=0)  # one full wave of CTAs per pass
+        sl.sl_enqueue_steps(bufs, dev_out, a.warmup, dtype=sl.SL_U32, cfg=cfg)
     else:
         for i in range(a.warmup):
-            sl.sl_enqueue(buf, dev_out[rb * i:], dtype=sl.SL_U32, cfg=cfg)
+            sl.sl_enqueue(bufs[i % 2], dev_out[rb * i:], dtype=sl.SL_U32, cfg=cfg)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -304,11 +310,11 @@ def run_ours(a):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
     ev[0].record(stream)
     if best.overlapped:
-        sl.sl_enqueue_steps(buf, dev_out[rb * a.warmup:], a.steps, dtype=sl.SL_U32, cfg=cfg)
+        sl.sl_enqueue_steps(bufs, dev_out[rb * a.warmup:], a.steps, dtype=sl.SL_U32, cfg=cfg)
         ev[a.steps].record(stream)
     else:
         for i in range(a.steps):
-            sl.sl_enqueue(buf, dev_out[rb * (a.warmup + i):], dtype=sl.SL_U32, cfg=cfg)
+            sl.sl_enqueue(bufs[i % 2], dev_out[rb * (a.warmup + i):], dtype=sl.SL_U32, cfg=cfg)
             ev[i + 1].record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -382,8 +388,10 @@ def run_ours(a):
         "config": {"workload": WORKLOAD, "bytes": nbytes, "choice": best.label(), "choice_spec": best.spec(),
                    "launch": "programmatic dependent launches (sl_enqueue_steps)" if best.overlapped
                    else "one sl_enqueue per step",
-                   "grid": best.grid_used, "resident_per_sm": best.resident,
-                   "l2": "inputs larger than L2 (4 GiB vs 129 MB): no flush between steps",
+                   "grid": best.resident * info["sm_count"] if best.overlapped else best.grid_used,
+                   "resident_per_sm": best.resident,
+                   "l2": "inputs larger than L2 (4 GiB vs 129 MB), two resident copies read alternately by "
+                         "consecutive steps: no flush between steps",
                    "parallelism": f"replicas x{world} (one buffer per GPU)"},
         "frac_of_datasheet": round(value / world / DATASHEET_GBS, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

@@ -235,20 +235,24 @@ int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_conf
                sl_result* dev_out);
 
 /* Enqueue `steps` (>= 1) back-to-back passes of one configuration on
- * cfg->stream, pass i writing its sl_result to dev_out[i] (DEVICE pointer,
- * 8-byte aligned, room for `steps` results).  Pass 0 is launched like
- * sl_enqueue; passes 1.. are programmatic dependent launches of the pass
- * before them: a pass's CTAs may start loading while the previous pass's last
- * CTAs are still running (the buffer is only read), and touch the library's
- * scratch only after that pass has completed -- so each pass's result is the
- * same as a separate sl_enqueue's, and the passes' ramp-up and tail overlap.
- * For the grid-stride traversals (SL_ASC / SL_DESC) of SL_LDG, SL_LDG4,
- * SL_LDG32, SL_CPASYNC and SL_LDSTS, with flush_l2 == 0; SL_DYN (whose chunk
- * claims use the scratch from the start) and SL_TMA (whose bounded waits may
- * write the error word at any time) are SL_ERR_ARG.  No paper counterpart:
- * the paper times one launch per cell. */
-int sl_enqueue_steps(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, int32_t steps,
-                     sl_result* dev_out);
+ * cfg->stream: pass i reads dev_bufs[i % nbufs] (nbufs >= 1 buffers of
+ * `bytes` each, e.g. two copies so that consecutive passes never read the
+ * same lines) and writes its sl_result to dev_out[i] (DEVICE pointer, 8-byte
+ * aligned, room for `steps` results).  Pass 0 is launched like sl_enqueue;
+ * passes 1.. are programmatic dependent launches of the pass before them: a
+ * pass's CTAs may start while the previous pass's last CTAs are still
+ * running (the buffers are only read), and touch the library's scratch only
+ * after that pass has completed -- so each pass's result is the same as a
+ * separate sl_enqueue's, and the passes' ramp-up and tail overlap.  Every
+ * pass runs one full wave (grid = resident CTAs per SM x SMs; cfg->grid must
+ * be 0 or that number), so a pass's CTAs get SM slots only as the previous
+ * pass's CTAs exit.  For the grid-stride traversals (SL_ASC / SL_DESC) of
+ * SL_LDG, SL_LDG4, SL_LDG32, SL_CPASYNC and SL_LDSTS, with flush_l2 == 0;
+ * SL_DYN (whose chunk claims use the scratch from the start) and SL_TMA
+ * (whose bounded waits may write the error word at any time) are
+ * SL_ERR_ARG.  No paper counterpart: the paper times one launch per cell. */
+int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes, int32_t dtype,
+                     const sl_config* cfg, int32_t steps, sl_result* dev_out);
 
 /* Sweep (paper §3 "Fixed-work control": run each K sweep ascending and
  * reversed; the warm-up launch is excluded as in §3 "Hardware counters").

@@ -146,14 +146,18 @@ def sl_enqueue(buf, dev_out, nbytes=None, dtype=SL_U32, cfg: sl_config | None = 
     _check(load().sl_enqueue(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), _addr(dev_out)))
 
 
-def sl_enqueue_steps(buf, dev_out, steps: int, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> None:
-    """`steps` back-to-back passes on cfg.stream, pass i's result to the i-th
-    RESULT_BYTES slot of the device buffer dev_out; passes after the first
-    are programmatic dependent launches (their start overlaps the previous
-    pass's tail)."""
+def sl_enqueue_steps(bufs, dev_out, steps: int, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> None:
+    """`steps` back-to-back passes on cfg.stream, pass i reading bufs[i %
+    len(bufs)] (one buffer or a list of equal-size buffers) and writing its
+    result to the i-th RESULT_BYTES slot of the device buffer dev_out; passes
+    after the first are programmatic dependent launches (their start overlaps
+    the previous pass's tail), each one full wave of CTAs."""
     cfg = cfg or config()
-    _check(load().sl_enqueue_steps(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), int(steps),
-                                   _addr(dev_out)))
+    if not isinstance(bufs, (list, tuple)):
+        bufs = [bufs]
+    arr = (ctypes.c_void_p * len(bufs))(*[_addr(b) for b in bufs])
+    _check(load().sl_enqueue_steps(arr, len(bufs), _nbytes(bufs[0], nbytes), _dtype(dtype), ctypes.byref(cfg),
+                                   int(steps), _addr(dev_out)))
 
 
 def sl_sweep(buf, cells, nbytes=None, dtype=SL_U32, repeats: int = 1, warmup: int = 1,

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <vector>
 #include <mutex>
 #include <tuple>
 
@@ -529,11 +530,12 @@ int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_conf
     return enqueue_locked(c, dev_buf, bytes, dtype, cfg, dev_out, false, nullptr);
 }
 
-int sl_enqueue_steps(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, int32_t steps,
-                     sl_result* dev_out) {
+int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes, int32_t dtype, const sl_config* cfg,
+                     int32_t steps, sl_result* dev_out) {
     if (!cfg) return fail(SL_ERR_ARG, "cfg is NULL");
     if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u)) return fail(SL_ERR_ARG, "dev_out NULL or misaligned");
     if (steps < 1) return fail(SL_ERR_ARG, "steps %d < 1", steps);
+    if (!dev_bufs || nbufs < 1) return fail(SL_ERR_ARG, "need at least one buffer");
     if (cfg->order != SL_ASC && cfg->order != SL_DESC)
         return fail(SL_ERR_ARG, "sl_enqueue_steps takes the SL_ASC / SL_DESC traversals only");
     if (cfg->mech == SL_TMA) return fail(SL_ERR_ARG, "sl_enqueue_steps does not take SL_TMA");
@@ -542,26 +544,42 @@ int sl_enqueue_steps(const void* dev_buf, uint64_t bytes, int32_t dtype, const s
     int rc = get_ctx(&c);
     if (rc) return rc;
     std::lock_guard<std::recursive_mutex> g(c->mu);
+    // One full wave: grid = resident CTAs per SM x SMs, so that a pass's CTAs
+    // get SM slots only as the previous pass's CTAs exit (the passes overlap
+    // in the tail, never side by side).
     Plan p;
-    rc = make_plan(c, dev_buf, bytes, dtype, cfg, &p);
+    sl_config full = *cfg;
+    full.grid = 0;
+    rc = make_plan(c, dev_bufs[0], bytes, dtype, &full, &p);
     if (rc) return rc;
-    if (p.grid == 0) {  // empty buffer (or no fixed iteration): zero results
+    const int32_t wave = p.resident * c->info.sm_count;
+    if (cfg->grid > 0 && cfg->grid != wave)
+        return fail(SL_ERR_ARG, "sl_enqueue_steps runs one full wave: grid must be 0 or %d (%d CTAs/SM x %d SMs)",
+                    wave, p.resident, c->info.sm_count);
+    full.grid = wave;
+    std::vector<Plan> plans(static_cast<size_t>(nbufs));
+    for (int32_t b = 0; b < nbufs; ++b) {
+        rc = make_plan(c, dev_bufs[b], bytes, dtype, &full, &plans[b]);
+        if (rc) return rc;
+    }
+    if (plans[0].grid == 0) {  // empty buffer (or no fixed iteration): zero results
         for (int32_t i = 0; i < steps; ++i) {
-            rc = enqueue_locked(c, dev_buf, bytes, dtype, cfg, dev_out + i, false, nullptr);
+            rc = enqueue_locked(c, dev_bufs[i % nbufs], bytes, dtype, &full, dev_out + i, false, nullptr);
             if (rc) return rc;
         }
         return SL_OK;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
-    rc = ensure_scratch(c, static_cast<uint64_t>(p.grid));
+    rc = ensure_scratch(c, static_cast<uint64_t>(plans[0].grid));
     if (rc) return rc;
-    p.args.parts = c->parts;
-    p.args.window = sl::ctrl_window(c->err);
-    p.args.err = sl::ctrl_err(c->err);
-    p.args.done = sl::ctrl_done(c->err);
     for (int32_t i = 0; i < steps; ++i) {
-        p.args.result = dev_out + i;
-        rc = launch(p, s, i > 0);
+        Plan& q = plans[i % nbufs];
+        q.args.parts = c->parts;
+        q.args.window = sl::ctrl_window(c->err);
+        q.args.err = sl::ctrl_err(c->err);
+        q.args.done = sl::ctrl_done(c->err);
+        q.args.result = dev_out + i;
+        rc = launch(q, s, i > 0);
         if (rc) return rc;
     }
     return SL_OK;

@@ -37,12 +37,15 @@ class Point:
     grid_used: int = 0
 
     def cfg(self, **kw):
+        """The point's sl_config; keyword arguments override its fields."""
         if self.mech == SL_TMA:
-            return config(self.mech, cta=self.cta, grid=self.grid, stage_bytes=self.stage_bytes,
-                          stages=self.stages, **kw)
-        if self.order and "order" not in kw:
-            kw["order"] = self.order
-        return config(self.mech, k=self.k, cta=self.cta, grid=self.grid, cop=self.cop, **kw)
+            base = dict(cta=self.cta, grid=self.grid, stage_bytes=self.stage_bytes, stages=self.stages)
+        else:
+            base = dict(k=self.k, cta=self.cta, grid=self.grid, cop=self.cop)
+            if self.order:
+                base["order"] = self.order
+        base.update(kw)
+        return config(self.mech, **base)
 
     @property
     def median(self) -> float:
@@ -146,24 +149,26 @@ def measure(buf, nbytes: int, points: list[Point], dtype: int = SL_U32, repeats:
     return points
 
 
-def measure_steps(buf, nbytes: int, points: list[Point], steps: int = 8, repeats: int = 3,
+def measure_steps(bufs, nbytes: int, points: list[Point], steps: int = 8, repeats: int = 3,
                   dtype: int = SL_U32) -> list[Point]:
-    """Throughput of `steps` back-to-back passes for every measured point:
-    one sl_enqueue_steps call (overlapped passes) where the point allows it,
-    else `steps` sl_enqueue calls; CUDA events on the current stream around
-    the passes, after one untimed round; median of `repeats` into step_gbs."""
+    """Throughput of `steps` back-to-back passes for every measured point,
+    pass i reading bufs[i % len(bufs)]: one sl_enqueue_steps call
+    (overlapped passes, one full wave of CTAs) where the point allows it, else
+    `steps` sl_enqueue calls; CUDA events on the current stream around the
+    passes, after one untimed round; median of `repeats` into step_gbs."""
     import torch
 
     from . import RESULT_BYTES, sl_enqueue, sl_enqueue_steps
+    bufs = list(bufs) if isinstance(bufs, (list, tuple)) else [bufs]
     out = torch.zeros(steps * RESULT_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def run(p, cfg):
         if p.overlapped:
-            sl_enqueue_steps(buf, out, steps, nbytes=nbytes, dtype=dtype, cfg=cfg)
+            sl_enqueue_steps(bufs, out, steps, nbytes=nbytes, dtype=dtype, cfg=p.cfg(grid=0))
         else:
             for i in range(steps):
-                sl_enqueue(buf, out[i * RESULT_BYTES:], nbytes=nbytes, dtype=dtype, cfg=cfg)
+                sl_enqueue(bufs[i % len(bufs)], out[i * RESULT_BYTES:], nbytes=nbytes, dtype=dtype, cfg=cfg)
 
     for p in points:
         if p.status != SL_OK or not p.gbs:

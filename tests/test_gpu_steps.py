@@ -41,7 +41,7 @@ def _results(sl, out, n):
 
 @pytest.mark.parametrize("mech,kw,loads", [
     ("ldg", dict(k=2, cta=256), 16), ("ldg", dict(k=6, cta=256, order="desc"), 16),
-    ("ldg", dict(k=4, cta=128, grid=10007), 16), ("ldg", dict(k=1, cta=1024, grid=152), 16),
+    ("ldg", dict(k=4, cta=128), 16), ("ldg", dict(k=1, cta=1024), 16),
     ("ldg32", dict(k=4, cta=256), 32), ("ldg4", dict(k=4, cta=256), 4),
     ("cpasync", dict(k=4, cta=256), 16), ("ldsts", dict(k=4, cta=256), 16),
 ])
@@ -55,6 +55,34 @@ def test_steps_each_pass_matches_oracle(sl, data, mech, kw, loads):
     for r in _results(sl, out, steps):
         assert (r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*want, want_loads, 0)
         assert r.window_ns > 0
+
+
+def test_steps_alternate_buffers(sl, data):
+    """Pass i reads buffer i mod 3: the per-pass checksums follow the
+    buffers."""
+    dev, host, want = data
+    other = torch.empty_like(dev)
+    sl.sl_fill_splitmix64(other, seed=7)
+    want7 = oracle.checksum(workloads.splitmix_u32(7, NBYTES // 4))
+    steps = 7
+    out = torch.zeros(steps * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps([dev, other, dev], out, steps, dtype=sl.SL_U32, cfg=sl.config("ldg", k=3, cta=256))
+    torch.cuda.synchronize()
+    for i, r in enumerate(_results(sl, out, steps)):
+        assert (r.sum_u32, r.xor_u64) == (want7 if i % 3 == 1 else want), i
+
+
+def test_steps_run_one_full_wave(sl, data):
+    dev, _, _ = data
+    cfg = sl.config("ldg", k=3, cta=256)
+    plan = sl.sl_plan(NBYTES, sl.SL_U32, cfg)
+    wave = plan.resident_per_sm * sl.sl_device_info()["sm_count"]
+    out = torch.zeros(2 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, 2, dtype=sl.SL_U32, cfg=sl.config("ldg", k=3, cta=256, grid=wave))
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_enqueue_steps(dev, out, 2, dtype=sl.SL_U32, cfg=sl.config("ldg", k=3, cta=256, grid=wave - 1))
+    assert e.value.status == sl.SL_ERR_ARG
+    torch.cuda.synchronize()
 
 
 def test_steps_interleaved_with_ordinary_launches(sl, data):
@@ -89,11 +117,12 @@ def test_steps_float_sums_equal_a_single_launch(sl):
 def test_steps_fixed_iteration(sl, data):
     dev, host, _ = data
     target = 2 * (NBYTES // 16) + 999
-    cfg = sl.config("ldg", k=4, cta=256, grid=608, target_loads=target)
+    cfg = sl.config("ldg", k=4, cta=256, target_loads=target)
+    wave = sl.sl_plan(NBYTES, sl.SL_U32, cfg).resident_per_sm * sl.sl_device_info()["sm_count"]
     out = torch.zeros(4 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     sl.sl_enqueue_steps(dev, out, 4, dtype=sl.SL_U32, cfg=cfg)
     torch.cuda.synchronize()
-    issued, _ = oracle.fixed_iteration(target, 608 * 256, [4])
+    issued, _ = oracle.fixed_iteration(target, wave * 256, [4])
     want = oracle.wrapped_checksum(host, issued[0])
     for r in _results(sl, out, 4):
         assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, issued[0])
