@@ -332,7 +332,7 @@ def run_ours(a):
     raw = dev_out.cpu().numpy().tobytes()
     res = [sl.sl_result.from_buffer_copy(raw[rb * i:rb * (i + 1)]) for i in range(a.warmup + a.steps)]
     ck = {(r.sum_u32, r.xor_u64, r.issued_loads, r.status) for r in res}
-    consistent = len(ck) == 1 and res[0].issued_loads == nbytes // 16 and res[0].status == 0
+    consistent = len(ck) == 1 and res[0].issued_loads == best.loads(nbytes) and res[0].status == 0
     per_rank = replicas.gather_results(res[-1].sum_u32, res[-1].xor_u64, res[-1].issued_loads, dist, device="cuda")
     ranks_agree = len(set(per_rank)) == 1
 

@@ -55,6 +55,11 @@ class Point:
     def step_median(self) -> float:
         return statistics.median(self.step_gbs) if self.step_gbs else 0.0
 
+    def loads(self, nbytes: int) -> int:
+        """Loads one pass over nbytes issues at this point's width (16-byte
+        loads; ceil(nbytes/32) for 32-byte loads)."""
+        return (nbytes + 31) // 32 if self.mech == SL_LDG32 else nbytes // 16
+
     @property
     def overlapped(self) -> bool:
         """Back-to-back passes run as programmatic dependent launches

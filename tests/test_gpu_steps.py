@@ -101,12 +101,13 @@ def test_steps_interleaved_with_ordinary_launches(sl, data):
 
 
 def test_steps_float_sums_equal_a_single_launch(sl):
-    """Same launch shape, same partial order: the float sum of every pass is
-    bit-identical to sl_run's."""
+    """Same launch shape (one full wave), same partial order: the float sum
+    of every pass is bit-identical to sl_run's at that grid."""
     x = workloads.payload(workloads.F32, (1 << 22) + 5 * 4)
     dev = torch.from_numpy(x.view(np.uint8)).cuda()
     cfg = sl.config("ldg", k=4, cta=256)
-    ref = sl.sl_run(dev, dtype=sl.SL_F32, cfg=cfg)
+    wave = sl.sl_plan(x.nbytes, sl.SL_F32, cfg).resident_per_sm * sl.sl_device_info()["sm_count"]
+    ref = sl.sl_run(dev, dtype=sl.SL_F32, cfg=sl.config("ldg", k=4, cta=256, grid=wave))
     out = torch.zeros(5 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     sl.sl_enqueue_steps(dev, out, 5, dtype=sl.SL_F32, cfg=cfg)
     torch.cuda.synchronize()

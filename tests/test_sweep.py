@@ -102,3 +102,24 @@ def test_fixed_mismatch_summary():
     (s,) = sweep.fixed_mismatch(rows)
     assert s["max_mismatch_pct"] == 0.024576
     assert s["issued"]["1"] == s["issued"]["2"] == 8138 * threads
+
+
+def test_tune_points_specs_loads_and_choice():
+    """Host logic of the point catalogue: specs round-trip, config overrides,
+    per-width load counts, overlap eligibility and the two choice rules."""
+    from paper_2608_15764_gb300 import SL_DYN, SL_LDG32, tune
+    pts = tune.default_points()
+    for p in pts:
+        q = tune.parse_point(p.spec())
+        assert (q.mech, q.k, q.cta, q.order, q.stage_bytes, q.stages) == \
+            (p.mech, p.k, p.cta, p.order, p.stage_bytes, p.stages), p.spec()
+    p = tune.parse_point("ldg32dyn:6:256")
+    assert p.mech == SL_LDG32 and p.order == SL_DYN and not p.overlapped
+    assert p.cfg(grid=0).grid == 0 and p.cfg().order == SL_DYN and p.cfg(order="asc").order == 0
+    assert p.loads(4096 + 16) == 129 and tune.parse_point("ldg:2:256").loads(4096 + 16) == 257
+    assert tune.parse_point("ldg:3:256").overlapped and not tune.parse_point("tma:16384:2:256").overlapped
+    a, b, c = tune.parse_point("ldg:2:256"), tune.parse_point("ldg:8:256"), tune.parse_point("tma:65536:2:256")
+    a.gbs, b.gbs, c.gbs = [7000.0], [7300.0], [7310.0]
+    a.step_gbs, b.step_gbs, c.step_gbs = [7500.0], [7400.0], []
+    assert tune.choose([a, b, c]) is b          # within 0.5% of the best: fewer bytes in flight
+    assert tune.choose([a, b, c], steps=True) is a
