@@ -5,7 +5,7 @@ Workload: a 4 GiB buffer of uint32 words from splitmix64(seed=1) (larger than
 the 129 MB L2, so no flush is needed between steps).  Before timing, the
 K-response curves of the mechanisms (LDG K at 16 and 32 bytes, grid-stride and
 dynamic chunks; cp.async D; TMA stage x stages) are measured on the same
-buffer as single launches, then every point's throughput over 8 back-to-back
+buffer as single launches, then every point's throughput over 16 back-to-back
 passes, and the fastest point for back-to-back passes is chosen
 (tune.choose(steps=True)).  One step = one checksum pass over the whole
 buffer with that point: one load kernel, whose last CTA to finish combines
@@ -279,7 +279,7 @@ def run_ours(a):
         choice = [0]
     elif rank == 0:
         tune.measure(buf, nbytes, points, repeats=a.curve_repeats, warmup=1)
-        tune.measure_steps(bufs, nbytes, points, steps=8, repeats=a.curve_repeats)
+        tune.measure_steps(bufs, nbytes, points, steps=16, repeats=a.curve_repeats)
         best = tune.choose(points, steps=True)
         choice = [points.index(best)]
     else:
