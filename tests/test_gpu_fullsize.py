@@ -1,8 +1,10 @@
 """Parity at the benchmark's full size: the 4 GiB uint32 splitmix64(seed=1)
 buffer, filled on the GPU, in every launch configuration the benchmark
-measures (its candidate set, from which it times the fastest), checked
+measures (its candidate set, from which it times the fastest, as single
+launches and as overlapped back-to-back passes over two copies), checked
 bit-exactly against the oracle's checksum of the same words generated on the
-host.  Also the 256 MiB LDG cells (K = 1, 2, 4, 8; 256 threads; 4 x SMs)."""
+host.  Also the 256 MiB LDG cells (K = 1, 2, 4, 8; 256 threads; 4 x SMs) and
+the allocation sweep's largest buffer (20 GiB)."""
 import os
 from concurrent.futures import ThreadPoolExecutor
 
@@ -67,3 +69,57 @@ def test_run_host_multi_chunk(sl):
                 sl.config("ldg", k=16, order="dyn", host_direct=True)]:
         r = sl.sl_run_host(pinned, dtype=sl.SL_U32, cfg=cfg)
         assert (r.sum_u32, r.xor_u64) == want and r.issued_loads == nbytes // 16
+
+
+def _oracle_generated(seed, nwords, chunk=1 << 26):
+    """The oracle's checksum of splitmix64 words [0, nwords), generated and
+    folded chunk by chunk on the host threads (no full host copy)."""
+    t = os.cpu_count() or 1
+    starts = list(range(0, nwords, chunk))
+
+    def one(s):
+        return oracle.checksum(workloads.splitmix_u32(seed, min(chunk, nwords - s), first_word=s))
+    with ThreadPoolExecutor(t) as ex:
+        return oracle.combine(ex.map(one, starts))
+
+
+def test_overlapped_passes_full_size(sl):
+    """The benchmark's timed launch configuration for grid-stride points:
+    back-to-back passes as programmatic dependent launches, one full wave per
+    pass, alternating between two resident 4 GiB copies."""
+    from paper_2608_15764_gb300 import tune
+    nbytes = 4 << 30
+    bufs = [torch.empty(nbytes, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    for b in bufs:
+        sl.sl_fill_splitmix64(b, seed=1)
+    want = _oracle_generated(1, nbytes // 4)
+    steps = 3
+    out = torch.zeros(steps * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    for p in [p for p in tune.default_points() if p.overlapped]:
+        sl.sl_enqueue_steps(bufs, out, steps, dtype=sl.SL_U32, cfg=p.cfg(grid=0))
+        torch.cuda.synchronize()
+        raw = out.cpu().numpy().tobytes()
+        for i in range(steps):
+            r = sl.sl_result.from_buffer_copy(raw[i * sl.RESULT_BYTES:(i + 1) * sl.RESULT_BYTES])
+            assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, p.loads(nbytes)), (p.label(), i)
+    del bufs
+    torch.cuda.empty_cache()
+
+
+def test_allocation_sweep_largest_size(sl):
+    """The allocation sweep's largest buffer (20 GiB, above L2 many times):
+    LDG K = 1, 2, 4, 8, 16 in both orders against the oracle."""
+    nbytes = 20 << 30
+    free, _ = torch.cuda.mem_get_info()
+    if free < nbytes + (2 << 30):
+        pytest.skip("not enough free device memory for a 20 GiB buffer")
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(dev, seed=1)
+    want = _oracle_generated(1, nbytes // 4)
+    sms = sl.sl_device_info()["sm_count"]
+    for k in (1, 2, 4, 8, 16):
+        for order in ("asc", "desc"):
+            r = sl.sl_run(dev, dtype=sl.SL_U32, cfg=sl.config("ldg", k=k, cta=256, grid=4 * sms, order=order))
+            assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, nbytes // 16), (k, order)
+    del dev
+    torch.cuda.empty_cache()
