@@ -300,6 +300,23 @@ typedef struct sl_chase_result {
 int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t warm, uint64_t hops, int32_t cache_l1,
              void* stream, sl_chase_result* out);
 
+/* ---- coverage audit ------------------------------------------------------ */
+
+/* As sl_run on a uint32 payload, but with the configuration's coverage
+ * instantiation: the same kernel and launch shape, where every load also
+ * adds 1 to dev_counts[i] for the 16-byte vector i it reads (a 32-byte load
+ * counts both of its vectors; cp.async counts at each copy, TMA at each bulk
+ * copy, per 16 bytes).  dev_counts: DEVICE array of bytes/16 uint32 counters,
+ * zeroed by the call.  Under exact fixed work every counter ends at `passes`;
+ * under the fixed-iteration control at q or q+1 (issued = q*n + r: the first r
+ * vectors q+1).  Instantiations exist for: SL_LDG K 1/3/8/16 grid-stride and
+ * K 2/12 SL_DYN at cta 128/256/512 (SL_COP_CG); SL_LDG32 K 1/3/8 at cta 256
+ * (grid-stride or SL_DYN); the fixed-iteration control at K 2/8, cta 256/1024;
+ * SL_CPASYNC D 1/4/16; SL_LDSTS G 1/16; SL_TMA (any ring) -- SL_ERR_ARG
+ * otherwise.  A debug tool (the counting atomics slow the kernel); no paper
+ * counterpart. */
+int sl_coverage(const void* dev_buf, uint64_t bytes, const sl_config* cfg, uint32_t* dev_counts, sl_result* out);
+
 /* ---- two co-resident streams in one CTA ---------------------------------- */
 
 typedef struct sl_twostream_result {

@@ -146,6 +146,16 @@ def sl_enqueue(buf, dev_out, nbytes=None, dtype=SL_U32, cfg: sl_config | None = 
     _check(load().sl_enqueue(_addr(buf), _nbytes(buf, nbytes), _dtype(dtype), ctypes.byref(cfg), _addr(dev_out)))
 
 
+def sl_coverage(buf, counts, nbytes=None, cfg: sl_config | None = None) -> sl_result:
+    """Coverage audit of a uint32 run: counts (a device array of nbytes/16
+    uint32, zeroed by the call) receives how many times each 16-byte vector
+    was loaded."""
+    cfg = cfg or config()
+    r = sl_result()
+    _check(load().sl_coverage(_addr(buf), _nbytes(buf, nbytes), ctypes.byref(cfg), _addr(counts), ctypes.byref(r)))
+    return r
+
+
 def sl_enqueue_steps(bufs, dev_out, steps: int, nbytes=None, dtype=SL_U32, cfg: sl_config | None = None) -> None:
     """`steps` back-to-back passes on cfg.stream, pass i reading bufs[i %
     len(bufs)] (one buffer or a list of equal-size buffers) and writing its

@@ -145,6 +145,7 @@ PROTOTYPES = {
     "sl_run_host": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), ctypes.POINTER(sl_result)]),
     "sl_run_noalloc": (_I32, [_P, _U64, _I32, ctypes.POINTER(sl_config), _P]),
     "sl_chase": (_I32, [_P, _U64, ctypes.c_uint32, _U64, _U64, _I32, _P, ctypes.POINTER(sl_chase_result)]),
+    "sl_coverage": (_I32, [_P, _U64, ctypes.POINTER(sl_config), _P, ctypes.POINTER(sl_result)]),
     "sl_enqueue_steps": (_I32, [ctypes.POINTER(ctypes.c_void_p), _I32, _U64, _I32, ctypes.POINTER(sl_config), _I32,
                                 _P]),
     "sl_twostream": (_I32, [_P, _U64, _P, _U64, _I32, _I32, _I32, _I32, _I32, _P,

@@ -409,12 +409,47 @@ void fill_shape(const Plan& p, sl_result* r) {
 }
 
 // Enqueue [flush], events, the load kernel and the combine on stream s.
+// The coverage instantiation matching cfg's kernel, or nullptr.
+const void* coverage_fn(const sl_config* cfg) {
+    const bool dyn = cfg->order == SL_DYN;
+    switch (cfg->mech) {
+    case SL_LDG:
+        if (cfg->target_loads) return sl::ldg_fixed_cov_kernel(cfg->k, cfg->cta);
+        return cfg->cop == SL_COP_CG ? sl::ldg_cov_kernel(cfg->k, cfg->cta, dyn) : nullptr;
+    case SL_LDG32: return sl::ldg32_cov_kernel(cfg->k, cfg->cta, dyn);
+    case SL_CPASYNC: return sl::cpasync_cov_kernel(cfg->k);
+    case SL_LDSTS: return sl::ldsts_cov_kernel(cfg->k);
+    case SL_TMA: return sl::tma_cov_kernel();
+    default: return nullptr;
+    }
+}
+
 int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
-                   sl_result* dev_out, bool events, Plan* plan_out) {
+                   sl_result* dev_out, bool events, Plan* plan_out, uint32_t* cov = nullptr) {
     Plan p;
     int rc = make_plan(c, buf, bytes, dtype, cfg, &p);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
+    if (cov) {
+        // coverage audit: the same launch shape with the counting instantiation
+        const void* fn = dtype == SL_U32 ? coverage_fn(cfg) : nullptr;
+        if (!fn)
+            return fail(SL_ERR_ARG, "no coverage instantiation for this configuration (uint32; LDG K 1/3/8/16 "
+                        "grid-stride or 2/12 SL_DYN at cta 128/256/512; SL_LDG32 K 1/3/8 at cta 256; "
+                        "fixed-iteration K 2/8 at cta 256/1024; cp.async D 1/4/16; SL_LDSTS G 1/16; TMA)");
+        FuncInfo* fi = nullptr;
+        rc = func_info(c, fn, p.smem, &fi);
+        if (rc) return rc;
+        if (fi->local_bytes > 0 || p.block > fi->max_threads)
+            return fail(SL_ERR_INFEASIBLE, "the coverage instantiation does not fit this launch shape");
+        int res = 0;
+        rc = occupancy(c, fn, p.block, p.smem, &res);
+        if (rc) return rc;
+        if (res < 1) return fail(SL_ERR_INFEASIBLE, "the coverage instantiation has zero occupancy");
+        p.fn = fn;
+        p.args.cov = cov;
+        CUDA_TRY(cudaMemsetAsync(cov, 0, (bytes / 16) * sizeof(uint32_t), s));
+    }
     rc = ensure_scratch(c, static_cast<uint64_t>(p.grid));
     if (rc) return rc;
     p.args.parts = c->parts;
@@ -434,9 +469,10 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
     return SL_OK;
 }
 
-int run_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out) {
+int run_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out,
+               uint32_t* cov = nullptr) {
     Plan p;
-    int rc = enqueue_locked(c, buf, bytes, dtype, cfg, c->dres, true, &p);
+    int rc = enqueue_locked(c, buf, bytes, dtype, cfg, c->dres, true, &p, cov);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
     CUDA_TRY(cudaMemcpyAsync(c->hres, c->dres, sizeof(sl_result), cudaMemcpyDeviceToHost, s));
@@ -528,6 +564,18 @@ int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_conf
     if (rc) return rc;
     std::lock_guard<std::recursive_mutex> g(c->mu);
     return enqueue_locked(c, dev_buf, bytes, dtype, cfg, dev_out, false, nullptr);
+}
+
+int sl_coverage(const void* dev_buf, uint64_t bytes, const sl_config* cfg, uint32_t* dev_counts, sl_result* out) {
+    if (!out || !cfg) return fail(SL_ERR_ARG, "NULL argument");
+    if (!dev_counts || (reinterpret_cast<uintptr_t>(dev_counts) & 3u))
+        return fail(SL_ERR_ARG, "dev_counts NULL or not 4-byte aligned");
+    if (cfg->mech == SL_LDG4) return fail(SL_ERR_ARG, "no coverage instantiation for SL_LDG4");
+    DevCtx* c = nullptr;
+    int rc = get_ctx(&c);
+    if (rc) return rc;
+    std::lock_guard<std::recursive_mutex> g(c->mu);
+    return run_locked(c, dev_buf, bytes, SL_U32, cfg, out, dev_counts);
 }
 
 int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes, int32_t dtype, const sl_config* cfg,

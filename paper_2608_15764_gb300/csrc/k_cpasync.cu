@@ -23,7 +23,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int D, int DT>
+template <int D, int DT, bool COV = false>
 __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
     extern __shared__ __align__(16) uint4 ring[];  // [D][cta]: slot k holds chunk k of a tile
     cta_start(a);
@@ -43,7 +43,10 @@ __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
         const uint64_t base = static_cast<uint64_t>(c.tile(a)) * tile_vec + threadIdx.x;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            if (base + static_cast<uint64_t>(k) * cta < nvec) cp_async16(my0 + k * stride, buf + base + k * cta);
+            if (base + static_cast<uint64_t>(k) * cta < nvec) {
+                cp_async16(my0 + k * stride, buf + base + k * cta);
+                cov_count<COV>(a, base + static_cast<uint64_t>(k) * cta);
+            }
             cp_async_commit();
         }
     }
@@ -70,7 +73,10 @@ __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
                 if (!cfull) acc.n += 1;
             }
             // refill slot k with chunk k of the next tile (an empty group at the end)
-            if (off < nrem) cp_async16(my0 + k * stride, np + off);
+            if (off < nrem) {
+                cp_async16(my0 + k * stride, np + off);
+                cov_count<COV>(a, (np + off) - buf);
+            }
             cp_async_commit();
             off += cta;
         }
@@ -102,6 +108,13 @@ static const void* cpasync_for(int d) {
     case 16: return reinterpret_cast<const void*>(&k_cpasync<16, DT>);
     default: return nullptr;
     }
+}
+
+const void* cpasync_cov_kernel(int d) {
+    if (d == 1) return reinterpret_cast<const void*>(&k_cpasync<1, SL_U32, true>);
+    if (d == 4) return reinterpret_cast<const void*>(&k_cpasync<4, SL_U32, true>);
+    if (d == 16) return reinterpret_cast<const void*>(&k_cpasync<16, SL_U32, true>);
+    return nullptr;
 }
 
 const void* cpasync_kernel(int dtype, int d) {

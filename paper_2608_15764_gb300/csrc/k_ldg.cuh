@@ -17,7 +17,7 @@
 
 namespace sl {
 
-template <int K, int CTA, int DT, int COP>
+template <int K, int CTA, int DT, int COP, bool COV = false>
 __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
     // launch_bounds(CTA, 1) lets ptxas keep all K loaded vectors in registers
     // (4K registers) instead of interleaving loads with folds to save
@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
             // K independent loads issued back to back, then consumed.
 #pragma unroll
             for (int k = 0; k < K; ++k) v[k] = ldg16<COP>(p + k * CTA);
+            if constexpr (COV) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) cov_count<COV>(a, (p + k * CTA) - buf);
+            }
 #pragma unroll
             for (int k = 0; k < K; ++k) acc.fold(v[k]);
             ++full_iters;
@@ -50,8 +54,12 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
             const uint32_t rem = static_cast<uint32_t>(a.nvec - static_cast<uint64_t>(tile) * TILE);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                if (threadIdx.x + k * CTA < rem) v[k] = ldg16<COP>(p + k * CTA);
-                else v[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (threadIdx.x + k * CTA < rem) {
+                    v[k] = ldg16<COP>(p + k * CTA);
+                    cov_count<COV>(a, (p + k * CTA) - buf);
+                } else {
+                    v[k] = make_uint4(0u, 0u, 0u, 0u);
+                }
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
 // Integer results are exact; float sums are correct to the same bound but not
 // bit-reproducible between runs, since a CTA's partial covers whichever
 // chunks it claimed.
-template <int K, int CTA, int DT>
+template <int K, int CTA, int DT, bool COV = false>
 __global__ void __launch_bounds__(CTA, 1) k_ldg_dyn(const KArgs a) {
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     __shared__ uint32_t slot[2];
@@ -103,6 +111,10 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg_dyn(const KArgs a) {
             uint4 v[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) v[k] = ldg16<SL_COP_CG>(p + k * CTA);
+            if constexpr (COV) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) cov_count<COV>(a, (p + k * CTA) - buf);
+            }
 #pragma unroll
             for (int k = 0; k < K; ++k) acc.fold(v[k]);
         }
@@ -112,8 +124,12 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg_dyn(const KArgs a) {
             uint4 v[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                if (threadIdx.x + k * CTA < rem) v[k] = ldg16<SL_COP_CG>(p + k * CTA);
-                else v[k] = make_uint4(0u, 0u, 0u, 0u);
+                if (threadIdx.x + k * CTA < rem) {
+                    v[k] = ldg16<SL_COP_CG>(p + k * CTA);
+                    cov_count<COV>(a, (p + k * CTA) - buf);
+                } else {
+                    v[k] = make_uint4(0u, 0u, 0u, 0u);
+                }
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) {

@@ -33,24 +33,28 @@ __device__ __forceinline__ Oct ldg32(const Oct* p) {
 
 // Guarded tail of a tile or chunk: units below n32 load 32 bytes, the unit
 // n32 itself (when the buffer ends in a half unit) loads the last 16 bytes.
-template <int K, int CTA, int DT>
-__device__ __forceinline__ void ragged32(const Oct* buf, uint64_t first, uint64_t n32, bool half, Acc<DT>& acc) {
+template <int K, int CTA, int DT, bool COV>
+__device__ __forceinline__ void ragged32(const KArgs& a, const Oct* buf, uint64_t first, uint64_t n32, bool half,
+                                         Acc<DT>& acc) {
 #pragma unroll 1
     for (int k = 0; k < K; ++k) {
         const uint64_t u = first + static_cast<uint64_t>(k) * CTA + threadIdx.x;
         if (u < n32) {
             const Oct v = ldg32(buf + u);
+            cov_count<COV>(a, 2 * u);
+            cov_count<COV>(a, 2 * u + 1);
             acc.fold(v.lo);
             acc.fold(v.hi);
             acc.n += 1;
         } else if (half && u == n32) {
             acc.fold(ldg16<SL_COP_CG>(reinterpret_cast<const uint4*>(buf + u)));
+            cov_count<COV>(a, 2 * u);
             acc.n += 1;
         }
     }
 }
 
-template <int K, int CTA, int DT>
+template <int K, int CTA, int DT, bool COV = false>
 __global__ void __launch_bounds__(CTA, 1) k_ldg32(const KArgs a) {
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     cta_start(a);
@@ -72,6 +76,13 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg32(const KArgs a) {
             Oct v[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) v[k] = ldg32(p + k * CTA);
+            if constexpr (COV) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    cov_count<COV>(a, 2 * static_cast<uint64_t>((p + k * CTA) - buf));
+                    cov_count<COV>(a, 2 * static_cast<uint64_t>((p + k * CTA) - buf) + 1);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 acc.fold(v[k].lo);
@@ -79,7 +90,7 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg32(const KArgs a) {
             }
             ++full_iters;
         } else {
-            ragged32<K, CTA, DT>(buf, static_cast<uint64_t>(tile) * TILE, n32, half, acc);
+            ragged32<K, CTA, DT, COV>(a, buf, static_cast<uint64_t>(tile) * TILE, n32, half, acc);
         }
     }
     acc.n += full_iters * K;
@@ -88,7 +99,7 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg32(const KArgs a) {
 
 // SL_DYN: chunks of a.tile_vec units claimed from *a.next (the next claim
 // prefetched by thread 0; one CTA barrier per chunk).
-template <int K, int CTA, int DT>
+template <int K, int CTA, int DT, bool COV = false>
 __global__ void __launch_bounds__(CTA, 1) k_ldg32_dyn(const KArgs a) {
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     __shared__ uint32_t slot[2];
@@ -121,6 +132,13 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg32_dyn(const KArgs a) {
             Oct v[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) v[k] = ldg32(p + k * CTA);
+            if constexpr (COV) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    cov_count<COV>(a, 2 * static_cast<uint64_t>((p + k * CTA) - buf));
+                    cov_count<COV>(a, 2 * static_cast<uint64_t>((p + k * CTA) - buf) + 1);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 acc.fold(v[k].lo);
@@ -128,7 +146,8 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg32_dyn(const KArgs a) {
             }
         }
         full_iters += nfull;
-        if (nfull * TILE < len) ragged32<K, CTA, DT>(buf, base + static_cast<uint64_t>(nfull) * TILE, n32, half, acc);
+        if (nfull * TILE < len)
+            ragged32<K, CTA, DT, COV>(a, buf, base + static_cast<uint64_t>(nfull) * TILE, n32, half, acc);
         __syncthreads();  // the prefetched claim is visible; the slot read next is not rewritten until j+2
         cur = vslot[(j + 1) & 1];
     }
@@ -177,6 +196,19 @@ static const void* ldg32_dt(int dtype, int k, int cta) {
 
 const void* ldg32_kernel(int dtype, int k, int cta, bool dyn) {
     return dyn ? ldg32_dt<true>(dtype, k, cta) : ldg32_dt<false>(dtype, k, cta);
+}
+
+const void* ldg32_cov_kernel(int k, int cta, bool dyn) {
+    if (cta != 256) return nullptr;
+    switch (k) {
+    case 1: return dyn ? reinterpret_cast<const void*>(&k_ldg32_dyn<1, 256, SL_U32, true>)
+                       : reinterpret_cast<const void*>(&k_ldg32<1, 256, SL_U32, true>);
+    case 3: return dyn ? reinterpret_cast<const void*>(&k_ldg32_dyn<3, 256, SL_U32, true>)
+                       : reinterpret_cast<const void*>(&k_ldg32<3, 256, SL_U32, true>);
+    case 8: return dyn ? reinterpret_cast<const void*>(&k_ldg32_dyn<8, 256, SL_U32, true>)
+                       : reinterpret_cast<const void*>(&k_ldg32<8, 256, SL_U32, true>);
+    default: return nullptr;
+    }
 }
 
 }  // namespace sl

@@ -18,7 +18,7 @@
 
 namespace sl {
 
-template <int K, int CTA>
+template <int K, int CTA, bool COV = false>
 __global__ void __launch_bounds__(CTA, 1) k_ldg_fixed(const KArgs a) {
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     cta_start(a);
@@ -39,12 +39,17 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg_fixed(const KArgs a) {
                 const uint4* p = buf + base + threadIdx.x;
 #pragma unroll
                 for (int k = 0; k < K; ++k) v[k] = ldg16<SL_COP_CG>(p + k * CTA);
+                if constexpr (COV) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) cov_count<COV>(a, (p + k * CTA) - buf);
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     uint64_t j = base + static_cast<uint64_t>(k) * CTA + threadIdx.x;
                     if (j >= nvec) j -= nvec;
                     v[k] = ldg16<SL_COP_CG>(buf + j);
+                    cov_count<COV>(a, j);
                 }
             }
 #pragma unroll
@@ -73,6 +78,14 @@ static const void* fixed_k(int k) {
     case 16: return reinterpret_cast<const void*>(&k_ldg_fixed<16, CTA>);
     default: return nullptr;
     }
+}
+
+const void* ldg_fixed_cov_kernel(int k, int cta) {
+    if (k == 2 && cta == 256) return reinterpret_cast<const void*>(&k_ldg_fixed<2, 256, true>);
+    if (k == 8 && cta == 256) return reinterpret_cast<const void*>(&k_ldg_fixed<8, 256, true>);
+    if (k == 2 && cta == 1024) return reinterpret_cast<const void*>(&k_ldg_fixed<2, 1024, true>);
+    if (k == 8 && cta == 1024) return reinterpret_cast<const void*>(&k_ldg_fixed<8, 1024, true>);
+    return nullptr;
 }
 
 const void* ldg_fixed_kernel(int dtype, int k, int cta) {

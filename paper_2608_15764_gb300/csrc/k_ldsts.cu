@@ -19,7 +19,7 @@ __device__ __forceinline__ void sts16(uint32_t saddr, const uint4& v) {
                  : "memory");
 }
 
-template <int G, int DT>
+template <int G, int DT, bool COV = false>
 __global__ void __launch_bounds__(G <= 8 ? 1024 : 256, 1) k_ldsts(const KArgs a) {
     extern __shared__ __align__(16) uint4 st_ring[];  // [G][cta]
     cta_start(a);
@@ -41,6 +41,10 @@ __global__ void __launch_bounds__(G <= 8 ? 1024 : 256, 1) k_ldsts(const KArgs a)
         if (base + tile_vec <= a.nvec) {
 #pragma unroll
             for (int g = 0; g < G; ++g) v[g] = ldg16<SL_COP_CG>(p + static_cast<size_t>(g) * cta);
+            if constexpr (COV) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) cov_count<COV>(a, (p + static_cast<size_t>(g) * cta) - buf);
+            }
 #pragma unroll
             for (int g = 0; g < G; ++g) sts16(my0 + g * stride, v[g]);
 #pragma unroll
@@ -54,6 +58,7 @@ __global__ void __launch_bounds__(G <= 8 ? 1024 : 256, 1) k_ldsts(const KArgs a)
             for (int g = 0; g < G; ++g) {
                 if (threadIdx.x + static_cast<uint64_t>(g) * cta < rem) {
                     sts16(my0 + g * stride, ldg16<SL_COP_CG>(p + static_cast<size_t>(g) * cta));
+                    cov_count<COV>(a, (p + static_cast<size_t>(g) * cta) - buf);
                     acc.fold(lds16(my0 + g * stride));
                     acc.n += 1;
                 }
@@ -85,6 +90,12 @@ static const void* ldsts_for(int g) {
     case 16: return reinterpret_cast<const void*>(&k_ldsts<16, DT>);
     default: return nullptr;
     }
+}
+
+const void* ldsts_cov_kernel(int g) {
+    if (g == 1) return reinterpret_cast<const void*>(&k_ldsts<1, SL_U32, true>);
+    if (g == 16) return reinterpret_cast<const void*>(&k_ldsts<16, SL_U32, true>);
+    return nullptr;
 }
 
 const void* ldsts_kernel(int dtype, int g) {

@@ -29,7 +29,7 @@
 
 namespace sl {
 
-template <int DT>
+template <int DT, bool COV = false>
 __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ __align__(8) uint64_t full[SL_MAX_STAGES];
@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
                 if (!((a.debug & SL_DEBUG_TMA_SKIP_STAGE) && i == 1)) {  // debug: leave chunk 1 unarmed
                     mbar_arrive_expect_tx(full0 + 8 * s, len);
                     bulk_g2s(ring0 + s * stage_bytes, gbuf + off, len, full0 + 8 * s);
+                    if constexpr (COV) {
+                        for (uint64_t v = off >> 4; v < (off + len) >> 4; ++v) cov_count<COV>(a, v);
+                    }
                     armed |= 1u << s;
                     last_par = (last_par & ~(1u << s)) | ((r & 1u) << s);
                 }
@@ -115,6 +118,8 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     // consumer warps fold (all lanes left the ring together); warp 0 does not
     cta_finish<DT>(acc, warp != 0, warp - 1, ncw, a);
 }
+
+const void* tma_cov_kernel() { return reinterpret_cast<const void*>(&k_tma<SL_U32, true>); }
 
 const void* tma_kernel(int dtype) {
     switch (dtype) {

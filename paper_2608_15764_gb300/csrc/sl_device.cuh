@@ -110,6 +110,14 @@ __device__ __forceinline__ float vec_sum(const uint4& v) {
     else return vec_sum_fp8(v);
 }
 
+// ---- coverage audit ------------------------------------------------------------
+// In the coverage instantiations (COV = true) every load of 16-byte vector i
+// also adds 1 to a.cov[i]; elsewhere this compiles to nothing.
+template <bool COV>
+__device__ __forceinline__ void cov_count(const KArgs& a, uint64_t i) {
+    if constexpr (COV) atomicAdd(a.cov + i, 1u);
+}
+
 // ---- the fold ----------------------------------------------------------------
 // Per-thread accumulator.  Integer part (every dtype): wraparound uint32 sum
 // of the four words and XOR of the two little-endian uint64 halves.  Float

@@ -43,6 +43,8 @@ struct KArgs {
                             // CTA resets it)
     uint32_t* next;         // SL_DYN traversal: next chunk to claim (zero before
                             // the launch; the last CTA resets it), else NULL
+    uint32_t* cov;          // coverage instantiations only: one counter per
+                            // 16-byte vector, +1 per load of it; else NULL
 };
 
 // Device error codes written to *err (first writer wins).
@@ -59,6 +61,16 @@ const void* tma_kernel(int dtype);
 const void* ldg4_kernel(int dtype, int k, int cta);
 const void* ldg32_kernel(int dtype, int k, int cta, bool dyn);
 const void* ldg_fixed_kernel(int dtype, int k, int cta);
+
+// Coverage instantiations (uint32 payloads, a subset of shapes): the same
+// kernels with every load also counted in KArgs::cov.  nullptr when the shape
+// has no coverage instantiation.
+const void* ldg_cov_kernel(int k, int cta, bool dyn);
+const void* ldg32_cov_kernel(int k, int cta, bool dyn);
+const void* ldg_fixed_cov_kernel(int k, int cta);
+const void* cpasync_cov_kernel(int d);
+const void* ldsts_cov_kernel(int g);
+const void* tma_cov_kernel();
 
 // Two co-resident streams in one CTA (k_two.cu).  Stream A = warps
 // [0, warps_a), stream B = the warps_b warps after them; one CTA per SM.
