@@ -48,6 +48,9 @@ GPU and checked against the first cell's checksum):
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
+  launches  paper §4.2 repeatability: the primary cell shape, K in {1,2,4,8},
+       as --repeats independent launches (each a sweep over K); per-launch
+       paired K=2 -> 8 change and the per-K spread across launches.
   two  paper §4.4: two co-resident plain-load streams in one CTA per SM,
        stream A = 1/2/4/8/16 warps, stream B = 0..16 warps, K = 1, 2, 4;
        displacement of A's bandwidth by B.
@@ -337,6 +340,55 @@ def run_ladder(out: str | None, verbose: bool = True):
     return rows
 
 
+def run_launches(out: str | None, launches: int = 10, gib: float = 4.0, verbose: bool = True):
+    """Paper §4.2 "Repeatability": the primary cell shape (one 1,024-thread
+    CTA per SM, .cg, 16-byte loads) on a 4 GiB buffer, run as `launches`
+    independent launches, each a sweep over K = 1, 2, 4, 8 (one timed run per
+    K after one warm-up run).  Per launch: GB/s per K and the paired K=2 -> 8
+    change; overall: the per-K spread across launches and the range of the
+    paired changes."""
+    import torch
+
+    import paper_2608_15764_gb300 as sl
+
+    sl.load()
+    sms = sl.sl_device_info()["sm_count"]
+    nbytes = int(gib * (1 << 30)) // 16 * 16
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    sl.sl_fill_splitmix64(buf, seed=1)
+    ks = (1, 2, 4, 8)
+    cfgs = [sl.config("ldg", k=k, cta=1024, grid=sms) for k in ks]
+    per = []
+    cks = set()
+    for li in range(launches):
+        res = sl.sl_sweep(buf, cfgs, dtype=sl.SL_U32, repeats=1, warmup=1)
+        gbs = {k: nbytes / row[0].device_ns for k, row in zip(ks, res)}
+        cks |= {(row[0].sum_u32, row[0].xor_u64, row[0].issued_loads) for row in res}
+        row = {"config": "launches", "launch": li, "gbs": {str(k): round(v, 2) for k, v in gbs.items()},
+               "paired_change_pct": round(decline(gbs[2], gbs[8]), 3)}
+        per.append(row)
+        if out:
+            with open(out, "a") as f:
+                f.write(json.dumps(row) + "\n")
+        if verbose:
+            print(json.dumps(row), flush=True)
+    spread = {}
+    for k in ks:
+        v = [r["gbs"][str(k)] for r in per]
+        med = statistics.median(v)
+        spread[str(k)] = {"median": round(med, 2), "spread_pct": round(100.0 * (max(v) - min(v)) / med, 3)}
+    changes = [r["paired_change_pct"] for r in per]
+    summary = {"config": "launches", "launches": launches, "per_k": spread,
+               "paired_change_pct": {"min": min(changes), "median": statistics.median(changes), "max": max(changes)},
+               "checksums_consistent": len(cks) == 1}
+    if out:
+        with open(out, "a") as f:
+            f.write(json.dumps(summary) + "\n")
+    if verbose:
+        print(json.dumps(summary), flush=True)
+    return per, summary
+
+
 TWO_WARPS = (1, 2, 4, 8, 16)
 TWO_B_WARPS = (0, 1, 2, 4, 8, 16)
 
@@ -498,12 +550,16 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
                     choices=["c1", "c2", "c2w", "fixedit", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
-                             "cpratio", "ladder", "k1gate", "two"])
+                             "cpratio", "ladder", "k1gate", "two", "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
     a = ap.parse_args(argv)
     t0 = time.time()
+    if a.config == "launches":
+        run_launches(a.out, launches=a.repeats)
+        print(json.dumps({"config": a.config, "seconds": round(time.time() - t0, 1)}), flush=True)
+        return 0
     if a.config == "two":
         rows = run_two(a.out, repeats=min(a.repeats, 5))
         print(json.dumps({"config": a.config, "cells": len(rows), "seconds": round(time.time() - t0, 1)}), flush=True)
