@@ -140,6 +140,11 @@ typedef struct sl_config {
 } sl_config;
 
 #define SL_DEBUG_TMA_SKIP_STAGE 1
+/* Experiment knob for SL_CPASYNC and SL_LDSTS: place the shared-memory ring n
+ * x 16 bytes (n = 0..7) past a 128-byte boundary instead of on it, to measure
+ * how the destination alignment of cp.async changes its L2 requests. */
+#define SL_DEBUG_SMEM_SKEW_SHIFT 8
+#define SL_DEBUG_SMEM_SKEW(n) (((n) & 7) << SL_DEBUG_SMEM_SKEW_SHIFT)
 
 /* ---- results ----------------------------------------------------------- */
 typedef struct sl_result {

@@ -18,7 +18,7 @@ import ctypes
 
 from ._abi import (  # noqa: F401  (re-exported constants)
     SL_ASC, SL_BF16, SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256, SL_CPASYNC,
-    SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_DYN, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
+    SL_DEBUG_SMEM_SKEW, SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_DYN, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
     SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_LDG4, SL_LDG32, SL_LDSTS, SL_MAX_D, SL_MAX_K,
     SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_TMA, SL_U32,
     STATUS_NAMES, RESULT_BYTES, load, sl_batch_desc, sl_chase_result, sl_config, sl_devinfo, sl_result,

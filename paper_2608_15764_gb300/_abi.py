@@ -31,6 +31,11 @@ SL_ASC, SL_DESC, SL_DYN = 0, 1, 2
 SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256 = 0, 1, 2
 SL_MAX_K, SL_MAX_D, SL_MIN_STAGES, SL_MAX_STAGES = 16, 16, 2, 8
 SL_DEBUG_TMA_SKIP_STAGE = 1
+SL_DEBUG_SMEM_SKEW_SHIFT = 8
+
+
+def SL_DEBUG_SMEM_SKEW(n: int) -> int:
+    return (int(n) & 7) << SL_DEBUG_SMEM_SKEW_SHIFT
 
 
 class sl_config(ctypes.Structure):

@@ -295,7 +295,8 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
                         cfg->k, SL_MAX_D);
         p->fn = cfg->mech == SL_CPASYNC ? sl::cpasync_kernel(dtype, cfg->k) : sl::ldsts_kernel(dtype, cfg->k);
         p->block = cta;
-        p->smem = static_cast<size_t>(cfg->k) * cta * 16;
+        p->smem = static_cast<size_t>(cfg->k) * cta * 16 +
+                  (((cfg->debug_flags >> SL_DEBUG_SMEM_SKEW_SHIFT) & 7) ? 128 : 0);  // room for a skewed ring
         tile_vec = static_cast<uint64_t>(cta) * cfg->k;
         p->warps = cta / 32;
         break;
@@ -373,7 +374,7 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     a.next = nullptr;  // set by the caller for SL_DYN
     a.nst = cfg->mech == SL_TMA ? cfg->stages : 0;
     a.debug = cfg->debug_flags;
-    a.timeout_ns = cfg->debug_flags ? DEBUG_TIMEOUT_NS : TIMEOUT_NS;
+    a.timeout_ns = (cfg->debug_flags & SL_DEBUG_TMA_SKIP_STAGE) ? DEBUG_TIMEOUT_NS : TIMEOUT_NS;
     return SL_OK;
 }
 

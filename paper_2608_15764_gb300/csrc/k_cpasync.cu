@@ -25,7 +25,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <int D, int DT, bool COV = false>
 __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
-    extern __shared__ __align__(16) uint4 ring[];  // [D][cta]: slot k holds chunk k of a tile
+    // [D][cta]: slot k holds chunk k of a tile.  128-byte aligned; an
+    // experiment flag (SL_DEBUG_SMEM_SKEW) can shift it by 16-byte steps.
+    extern __shared__ __align__(128) uint4 ring[];
     cta_start(a);
     const uint32_t cta = blockDim.x;
     const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
@@ -33,7 +35,8 @@ __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
     const uint32_t total = static_cast<uint32_t>(a.total);
     const uint64_t nvec = a.nvec;
     const uint64_t tile_vec = static_cast<uint64_t>(cta) * D;
-    const uint32_t my0 = smem_addr(ring + threadIdx.x), stride = cta * 16u;
+    const uint32_t skew = (static_cast<uint32_t>(a.debug) >> SL_DEBUG_SMEM_SKEW_SHIFT) & 7u;
+    const uint32_t my0 = smem_addr(ring + skew + threadIdx.x), stride = cta * 16u;
     Acc<DT> acc;
     uint32_t full_tiles = 0;
     TileCursor c;

@@ -21,14 +21,15 @@ __device__ __forceinline__ void sts16(uint32_t saddr, const uint4& v) {
 
 template <int G, int DT, bool COV = false>
 __global__ void __launch_bounds__(G <= 8 ? 1024 : 256, 1) k_ldsts(const KArgs a) {
-    extern __shared__ __align__(16) uint4 st_ring[];  // [G][cta]
+    extern __shared__ __align__(128) uint4 st_ring[];  // [G][cta]; 128-byte aligned (+ SL_DEBUG_SMEM_SKEW)
     cta_start(a);
     const uint32_t cta = blockDim.x;
     const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
     const uint32_t ntiles = static_cast<uint32_t>(a.ntiles);
     const uint32_t total = static_cast<uint32_t>(a.total);
     const uint64_t tile_vec = static_cast<uint64_t>(cta) * G;
-    const uint32_t my0 = smem_addr(st_ring + threadIdx.x), stride = cta * 16u;
+    const uint32_t skew = (static_cast<uint32_t>(a.debug) >> SL_DEBUG_SMEM_SKEW_SHIFT) & 7u;
+    const uint32_t my0 = smem_addr(st_ring + skew + threadIdx.x), stride = cta * 16u;
     Acc<DT> acc;
     uint32_t full_iters = 0;
     TileCursor c;

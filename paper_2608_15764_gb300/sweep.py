@@ -40,6 +40,9 @@ GPU and checked against the first cell's checksum):
   c2w  the residency grid of c2 at the other two load widths: 4-byte loads
        (K in {1,2,4,8,16}) and 32-byte loads (K in {1,2,3,4,6,8}); with c2
        it gives the paper's regime map over warps x width.
+  cpskew  cp.async D in {1,2,4,8} and the matched LDG->STS kernel (G=4) with the
+       shared-memory ring 0, 16, 32 or 64 bytes past a 128-byte boundary
+       (SL_DEBUG_SMEM_SKEW), 1 GiB: the destination alignment's effect.
   fixedit  the paper's own fixed-iteration control (§3, §4.2): the primary
        cell shape (1,024-thread CTAs, .cg, 16 B) issuing 16,785 MiB of loads
        that wrap around a 512 MiB or 4 GiB allocation, at 132 CTAs (the
@@ -92,6 +95,13 @@ def _cells(config: str, sms: int):
             for r in range(1, 9):
                 for k in (1, 2, 3, 4, 6, 8, 12, 16):
                     yield dict(mech="ldg", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
+    elif config == "cpskew":
+        # destination alignment of the shared-memory ring: 0 = 128-byte
+        # aligned, n = n x 16 bytes past a 128-byte boundary
+        for skew in (0, 1, 2, 4):
+            for d in (1, 2, 4, 8):
+                yield dict(mech="cpasync", k=d, cta=256, grid=0, skew=skew, gib=1)
+            yield dict(mech="ldsts", k=4, cta=256, grid=0, skew=skew, gib=1)
     elif config == "fixedit":
         # paper §3 / §4.2: the primary cell under the paper's own fixed-iteration
         # control (16,785 MiB of 16-byte loads, wrapping over the allocation),
@@ -225,7 +235,8 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
             cfgs, keep = [], []
             for c in seq:
                 passes = c.get("passes", 1)
-                kw = dict(cta=c["cta"], grid=c["grid"], passes=passes, target_loads=c.get("target_loads", 0))
+                kw = dict(cta=c["cta"], grid=c["grid"], passes=passes, target_loads=c.get("target_loads", 0),
+                          debug_flags=sl.SL_DEBUG_SMEM_SKEW(c.get("skew", 0)))
                 if c["mech"] == "tma":
                     cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
                 else:
@@ -549,7 +560,7 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c2w", "fixedit", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
+                    choices=["c1", "c2", "c2w", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
                              "cpratio", "ladder", "k1gate", "two", "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)

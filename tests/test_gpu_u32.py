@@ -153,6 +153,17 @@ def test_ldg4_small_ragged_and_passes(sl, data, nvec, k):
         assert r.issued_loads == passes * nbytes // 4
 
 
+@pytest.mark.parametrize("mech,k", [("cpasync", 1), ("cpasync", 4), ("cpasync", 16), ("ldsts", 4), ("ldsts", 16)])
+@pytest.mark.parametrize("skew", [1, 2, 4, 7])
+def test_smem_skew_keeps_results(sl, data, mech, k, skew):
+    """The ring-alignment experiment knob moves the shared-memory slots only."""
+    dev, _, want = data
+    r = sl.sl_run(dev, nbytes=NBYTES, dtype=sl.SL_U32,
+                  cfg=sl.config(mech, k=k, cta=256, debug_flags=sl.SL_DEBUG_SMEM_SKEW(skew)))
+    assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, NBYTES // 16)
+    assert r.smem_bytes == k * 256 * 16 + 128
+
+
 def test_ldg4_rejects_other_forms(sl, data):
     dev, _, _ = data
     for kw, dtype, code in [(dict(k=3), sl.SL_U32, sl.SL_ERR_ARG), (dict(k=1, cta=32), sl.SL_U32, sl.SL_ERR_ARG),
