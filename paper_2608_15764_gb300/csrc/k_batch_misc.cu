@@ -18,7 +18,7 @@ __device__ __forceinline__ void kb_cp_wait() { asm volatile("cp.async.wait_group
 // folds (as k_cpasync).  The pipeline drains at the end of each item.
 template <int D, int DT>
 __global__ void __launch_bounds__(1024) kb_cpasync(const BArgs a) {
-    extern __shared__ __align__(16) uint4 cp_ring[];  // [D][cta]
+    extern __shared__ __align__(128) uint4 cp_ring[];  // [D][cta], 128-byte aligned (cp.async destinations)
     __shared__ uint32_t slot;
     const uint32_t cta = blockDim.x, t = threadIdx.x;
     const uint32_t my0 = smem_addr(cp_ring + t), stride = cta * 16u;
