@@ -129,7 +129,7 @@ def combine(parts) -> tuple[int, int]:
 
 
 def issued_loads(nbytes: int, passes: int = 1) -> int:
-    """Issued 16-byte logical loads under the build's fixed-work control."""
+    """Issued 16-byte logical loads under the library's fixed-work control."""
     return int(_load().oracle_issued_loads(nbytes, passes))
 
 

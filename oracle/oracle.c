@@ -18,7 +18,7 @@
  *    the allocation, so the buffer is re-read).
  *
  *  - Paper §3 "Fixed-work control" and §4.2 "Exact-work accounting": issued
- *    logical loads.  The build's control issues exactly bytes/16 sixteen-byte
+ *    logical loads.  The library's control issues exactly bytes/16 sixteen-byte
  *    loads per pass at every K; the paper's own fixed-iteration arithmetic
  *    (iterations = floor(L / (threads*K))) and its mismatch are also given so
  *    the printed 0.024576% can be reconstructed.
@@ -105,7 +105,7 @@ void oracle_wrapped_checksum(const uint32_t *w, uint64_t nwords, uint64_t nloads
 
 /* ---- issued-load accounting ------------------------------------------- */
 
-/* The build's fixed-work control: one 16-byte logical load per 16 bytes per
+/* The library's fixed-work control: one 16-byte logical load per 16 bytes per
  * pass, independent of K, mechanism, CTA shape, grid and order. */
 uint64_t oracle_issued_loads(uint64_t bytes, uint64_t passes)
 {

@@ -1,6 +1,6 @@
 // k_chase.cu -- the pointer-chase latency probe (paper §4.1 "Primitive
 // baseline": unloaded latency on a single SM from a dependent pointer chain,
-// .ca and .cg; NEXT row of the build's scope).
+// .ca and .cg).
 //
 // One thread follows the chain: idx = chain[idx].  Each load's address depends
 // on the previous load's value, so exactly one load is in flight.  A first

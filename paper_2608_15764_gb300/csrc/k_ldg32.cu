@@ -2,7 +2,7 @@
 //
 // The paper sweeps load width as well as K (§3: 4- and 16-byte cells; its
 // regime map is over warps x width).  sm_100-class GPUs add 256-bit global
-// loads (ld.global.v8.u32), so this build adds a 32-byte width: K independent
+// loads (ld.global.v8.u32), so the library adds a 32-byte width: K independent
 // 32-byte loads per thread per iteration, issued before any is consumed; one
 // warp instruction reads 1,024 contiguous bytes.
 //
