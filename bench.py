@@ -180,6 +180,16 @@ def host_buffer(nbytes: int, pinned: bool):
     return t
 
 
+def _roofline_simple(achieved: float, note: str) -> dict:
+    """The HBM roofline object for a workload line without per-kernel DRAM
+    counters (traffic null)."""
+    peak, kind = _peaks()
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "peak_kind": f"{kind} copy (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "fallback",
+            "traffic": None, "traffic_note": "no DRAM counters taken for this workload", "note": note}
+
+
 def cpu_oracle(words, seconds: float):
     """Time the CPU oracle on all host cores over repeated full passes of the
     workload (each pass split into one contiguous range per thread; the
@@ -538,6 +548,8 @@ def run_batch(a):
                              "cores": threads, "kind": "oracle",
                              "sample": "the oracle's uint32 checksum of all 1,024 buffers per dtype, "
                                        "buffers spread over the host threads"},
+            "roofline": _roofline_simple(value, "aggregate bytes of all buffers / CUDA-event time of the graph "
+                                                "launch (all class kernels and the combine)"),
             "per_dtype": per,
             "parity": all(p["checksums_match_oracle"] for p in per) and
             all(p["fsum_max_gated_err_sample48"] is None or p["fsum_max_gated_err_sample48"] <= 2e-6 for p in per)}
@@ -625,6 +637,8 @@ def run_prec(a):
             "cpu_baseline": {"value": round(len(cpu) / sum(1.0 / v for v in cpu), 2), "unit": "GB/s",
                              "cores": threads, "kind": "oracle",
                              "sample": "one FP64 Neumaier pass over each full payload, split over the host threads"},
+            "roofline": _roofline_simple(value, "harmonic mean over dtypes of the fastest point's bytes / "
+                                                "CUDA-event time of one launch"),
             "per_dtype": per, "max_gated_err": worst_all, "parity": worst_all <= 2e-6}
     print(json.dumps(line), flush=True)
     if a.out:
