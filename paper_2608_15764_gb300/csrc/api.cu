@@ -52,13 +52,17 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
+// On failure: record the message, clear the runtime's last-error state (so a
+// later launch check does not report this error again) and return the status.
 #define CUDA_TRY(expr)                                                                        \
     do {                                                                                      \
         cudaError_t e_ = (expr);                                                              \
-        if (e_ != cudaSuccess)                                                                \
+        if (e_ != cudaSuccess) {                                                              \
+            (void)cudaGetLastError();                                                         \
             return fail(e_ == cudaErrorMemoryAllocation ? SL_ERR_OOM : SL_ERR_CUDA,           \
                         "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,     \
                         __LINE__);                                                            \
+        }                                                                                     \
     } while (0)
 
 struct FuncInfo {
