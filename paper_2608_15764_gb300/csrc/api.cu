@@ -41,6 +41,7 @@ constexpr uint64_t TIMEOUT_NS = 2000000000ull;     // per-wait bound, normal run
 constexpr uint64_t DEBUG_TIMEOUT_NS = 50000000ull;  // per-wait bound, fault-injection runs
 constexpr int64_t MAX_GRID = 1 << 20;
 constexpr uint64_t DYN_CHUNK_VEC = 65536;          // SL_DYN chunk: 1 MiB of 16-byte vectors
+constexpr int32_t STEP_COUNTERS = 4096;            // sl_enqueue_steps: SL_DYN passes per counter segment
 
 thread_local char g_err[1024] = "";
 
@@ -83,6 +84,7 @@ struct DevCtx {
     sl_result* hres = nullptr;  // pinned host copy
     uint64_t* two_dev = nullptr;   // sl_twostream: timer words [0, 8) and results [8, 24)
     uint64_t* two_host = nullptr;  // pinned copy of the results
+    uint32_t* step_next = nullptr; // sl_enqueue_steps with SL_DYN: one chunk counter per pass
     void* flush = nullptr;
     uint64_t flush_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -589,8 +591,7 @@ int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes,
     if (!dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 7u)) return fail(SL_ERR_ARG, "dev_out NULL or misaligned");
     if (steps < 1) return fail(SL_ERR_ARG, "steps %d < 1", steps);
     if (!dev_bufs || nbufs < 1) return fail(SL_ERR_ARG, "need at least one buffer");
-    if (cfg->order != SL_ASC && cfg->order != SL_DESC)
-        return fail(SL_ERR_ARG, "sl_enqueue_steps takes the SL_ASC / SL_DESC traversals only");
+    const bool dyn = cfg->order == SL_DYN;
     if (cfg->mech == SL_TMA) return fail(SL_ERR_ARG, "sl_enqueue_steps does not take SL_TMA");
     if (cfg->flush_l2) return fail(SL_ERR_ARG, "sl_enqueue_steps takes flush_l2 == 0");
     DevCtx* c = nullptr;
@@ -625,14 +626,24 @@ int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes,
     cudaStream_t s = static_cast<cudaStream_t>(cfg->stream);
     rc = ensure_scratch(c, static_cast<uint64_t>(plans[0].grid));
     if (rc) return rc;
+    if (dyn && !c->step_next) CUDA_TRY(cudaMalloc(&c->step_next, STEP_COUNTERS * sizeof(uint32_t)));
     for (int32_t i = 0; i < steps; ++i) {
+        // SL_DYN claims chunks from its counter from its first instruction, so
+        // every pass gets a counter of its own, zeroed (in stream order, before
+        // the segment's first pass) for up to STEP_COUNTERS passes at a time;
+        // a segment's first pass is an ordinary launch.
+        const int32_t slot = i % STEP_COUNTERS;
+        if (dyn && slot == 0)
+            CUDA_TRY(cudaMemsetAsync(c->step_next, 0,
+                                     std::min<int32_t>(STEP_COUNTERS, steps - i) * sizeof(uint32_t), s));
         Plan& q = plans[i % nbufs];
         q.args.parts = c->parts;
         q.args.window = sl::ctrl_window(c->err);
         q.args.err = sl::ctrl_err(c->err);
         q.args.done = sl::ctrl_done(c->err);
+        q.args.next = dyn ? c->step_next + slot : nullptr;
         q.args.result = dev_out + i;
-        rc = launch(q, s, i > 0);
+        rc = launch(q, s, i > 0 && !(dyn && slot == 0));
         if (rc) return rc;
     }
     return SL_OK;

@@ -63,8 +63,8 @@ class Point:
     @property
     def overlapped(self) -> bool:
         """Back-to-back passes run as programmatic dependent launches
-        (sl_enqueue_steps): grid-stride traversals of every mechanism but TMA."""
-        return self.mech != SL_TMA and self.order != 2
+        (sl_enqueue_steps): every mechanism but TMA."""
+        return self.mech != SL_TMA
 
     @property
     def offered(self) -> int:

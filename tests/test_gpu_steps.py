@@ -44,6 +44,8 @@ def _results(sl, out, n):
     ("ldg", dict(k=4, cta=128), 16), ("ldg", dict(k=1, cta=1024), 16),
     ("ldg32", dict(k=4, cta=256), 32), ("ldg4", dict(k=4, cta=256), 4),
     ("cpasync", dict(k=4, cta=256), 16), ("ldsts", dict(k=4, cta=256), 16),
+    ("ldg", dict(k=12, cta=256, order="dyn"), 16), ("ldg", dict(k=2, cta=512, order="dyn"), 16),
+    ("ldg32", dict(k=6, cta=256, order="dyn"), 32),
 ])
 def test_steps_each_pass_matches_oracle(sl, data, mech, kw, loads):
     dev, _, want = data
@@ -136,8 +138,33 @@ def test_steps_empty_and_rejected(sl, data):
     torch.cuda.synchronize()
     for r in _results(sl, out, 3):
         assert (r.sum_u32, r.xor_u64, r.issued_loads) == (0, 0, 0)
-    for cfg, steps in [(sl.config("ldg", order="dyn"), 2), (sl.config("tma"), 2),
-                       (sl.config("ldg", flush_l2=True), 2), (sl.config("ldg"), 0)]:
+    for cfg, steps in [(sl.config("tma"), 2), (sl.config("ldg", flush_l2=True), 2), (sl.config("ldg"), 0)]:
         with pytest.raises(sl.SLError) as e:
             sl.sl_enqueue_steps(dev, out, steps, dtype=sl.SL_U32, cfg=cfg)
         assert e.value.status == sl.SL_ERR_ARG
+
+
+def test_dynamic_steps_across_counter_segments(sl, data):
+    """More passes than one segment of per-pass chunk counters (4,096): every
+    pass still covers the buffer once."""
+    dev, _, want = data
+    steps = 4096 + 7
+    nb = 16 * 70001  # a small buffer: many short passes
+    host = workloads.splitmix_u32(SEED, nb // 4)
+    want = oracle.checksum(host)
+    out = torch.zeros(steps * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, steps, nbytes=nb, dtype=sl.SL_U32, cfg=sl.config("ldg", k=4, order="dyn"))
+    torch.cuda.synchronize()
+    for r in _results(sl, out, steps):
+        assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, nb // 16)
+
+
+def test_dynamic_steps_float_sums(sl):
+    x = workloads.payload(workloads.BF16, (1 << 23) + 8 * 7)
+    dev = torch.from_numpy(x.view(np.uint8)).cuda()
+    ref, absum = oracle.fsum(workloads.BF16, x)
+    out = torch.zeros(6 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    sl.sl_enqueue_steps(dev, out, 6, dtype=sl.SL_BF16, cfg=sl.config("ldg", k=8, order="dyn"))
+    torch.cuda.synchronize()
+    for r in _results(sl, out, 6):
+        assert abs(r.fsum - ref) <= 2e-6 * abs(ref)

@@ -114,7 +114,7 @@ def test_tune_points_specs_loads_and_choice():
         assert (q.mech, q.k, q.cta, q.order, q.stage_bytes, q.stages) == \
             (p.mech, p.k, p.cta, p.order, p.stage_bytes, p.stages), p.spec()
     p = tune.parse_point("ldg32dyn:6:256")
-    assert p.mech == SL_LDG32 and p.order == SL_DYN and not p.overlapped
+    assert p.mech == SL_LDG32 and p.order == SL_DYN and p.overlapped
     assert p.cfg(grid=0).grid == 0 and p.cfg().order == SL_DYN and p.cfg(order="asc").order == 0
     assert p.loads(4096 + 16) == 129 and tune.parse_point("ldg:2:256").loads(4096 + 16) == 257
     assert tune.parse_point("ldg:3:256").overlapped and not tune.parse_point("tma:16384:2:256").overlapped
