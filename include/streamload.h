@@ -251,12 +251,12 @@ int sl_enqueue(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_conf
  * separate sl_enqueue's, and the passes' ramp-up and tail overlap.  Every
  * pass runs one full wave (grid = resident CTAs per SM x SMs; cfg->grid must
  * be 0 or that number), so a pass's CTAs get SM slots only as the previous
- * pass's CTAs exit.  For SL_LDG, SL_LDG4, SL_LDG32, SL_CPASYNC and SL_LDSTS
- * in every traversal they have (SL_DYN passes claim chunks from a counter of
- * their own, zeroed in stream order before every 4,096 passes, where one
- * ordinary launch restarts the overlap), with flush_l2 == 0; SL_TMA (whose
- * bounded waits may write the error word at any time) is SL_ERR_ARG.  No
- * paper counterpart: the paper times one launch per cell. */
+ * pass's CTAs exit.  Every mechanism and traversal (SL_DYN passes claim
+ * chunks from a counter of their own, zeroed in stream order before every
+ * 4,096 passes, where one ordinary launch restarts the overlap; SL_TMA
+ * publishes a bounded wait's error only when the CTA finishes), with
+ * flush_l2 == 0.  No paper counterpart: the paper times one launch per
+ * cell. */
 int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes, int32_t dtype,
                      const sl_config* cfg, int32_t steps, sl_result* dev_out);
 

@@ -592,7 +592,6 @@ int sl_enqueue_steps(const void* const* dev_bufs, int32_t nbufs, uint64_t bytes,
     if (steps < 1) return fail(SL_ERR_ARG, "steps %d < 1", steps);
     if (!dev_bufs || nbufs < 1) return fail(SL_ERR_ARG, "need at least one buffer");
     const bool dyn = cfg->order == SL_DYN;
-    if (cfg->mech == SL_TMA) return fail(SL_ERR_ARG, "sl_enqueue_steps does not take SL_TMA");
     if (cfg->flush_l2) return fail(SL_ERR_ARG, "sl_enqueue_steps takes flush_l2 == 0");
     DevCtx* c = nullptr;
     int rc = get_ctx(&c);

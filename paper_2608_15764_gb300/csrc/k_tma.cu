@@ -18,8 +18,9 @@
 // t+cta, ...) and fold.  No multicast is used anywhere.
 //
 // Every wait is bounded: a wait that exceeds a.timeout_ns (by %globaltimer)
-// or a hard iteration cap records an error code in *a.err, raises the CTA's
-// abort flag and returns false.  Waiters also give up when they see the abort
+// or a hard iteration cap records an error code in the CTA's shared error word
+// (published to *a.err when the CTA finishes, after any previous launch on
+// the stream has completed), raises the CTA's abort flag and returns false.  Waiters also give up when they see the abort
 // flag.  Before exiting after an abort, the producer waits (bounded) for
 // every bulk copy it issued to land (it does so on every exit), so no copy is
 // in flight into shared memory when the CTA exits.  A consumer warp leaves
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     __shared__ __align__(8) uint64_t full[SL_MAX_STAGES];
     __shared__ __align__(8) uint64_t empty[SL_MAX_STAGES];
     __shared__ volatile int abort_flag;
+    __shared__ uint32_t cta_err;  // a bounded wait's error code, published to *a.err by cta_finish
 
     cta_start(a);
     const uint32_t nst = static_cast<uint32_t>(a.nst);
@@ -51,6 +53,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     if (threadIdx.x == 0) {
         ring_init(full0, empty0, nst, ncw);
         abort_flag = 0;
+        cta_err = 0;
     }
     __syncthreads();
 
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
             c.start(ntiles);
             uint32_t s = 0, r = 0;  // stage and round of chunk i = r*nst + s
             for (uint32_t i = 0; c.it < total; c.next(ntiles), ++i) {
-                if (r > 0 && !bounded_wait(empty0 + 8 * s, (r - 1) & 1u, a.err, a.timeout_ns, &abort_flag, true,
+                if (r > 0 && !bounded_wait(empty0 + 8 * s, (r - 1) & 1u, &cta_err, a.timeout_ns, &abort_flag, true,
                                            DEV_ERR_TIMEOUT_EMPTY))
                     break;
                 const uint64_t off = static_cast<uint64_t>(c.tile(a)) * stage_bytes;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
             {
                 for (uint32_t s = 0; s < nst; ++s)
                     if (armed & (1u << s))
-                        bounded_wait(full0 + 8 * s, (last_par >> s) & 1u, a.err, a.timeout_ns, &abort_flag,
+                        bounded_wait(full0 + 8 * s, (last_par >> s) & 1u, &cta_err, a.timeout_ns, &abort_flag,
                                      false, DEV_ERR_TIMEOUT_DRAIN);
             }
         }
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
         uint32_t s = 0, r = 0;
         for (; c.it < total; c.next(ntiles)) {
             const bool got =
-                bounded_wait(full0 + 8 * s, r & 1u, a.err, a.timeout_ns, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
+                bounded_wait(full0 + 8 * s, r & 1u, &cta_err, a.timeout_ns, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
             if (!__all_sync(FULL_MASK, got)) break;  // warp-uniform exit
             const uint64_t off = static_cast<uint64_t>(c.tile(a)) * stage_bytes;
             const uint64_t left = bytes - off;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
         }
     }
     // consumer warps fold (all lanes left the ring together); warp 0 does not
-    cta_finish<DT>(acc, warp != 0, warp - 1, ncw, a);
+    cta_finish<DT>(acc, warp != 0, warp - 1, ncw, a, &cta_err);
 }
 
 const void* tma_cov_kernel() { return reinterpret_cast<const void*>(&k_tma<SL_U32, true>); }

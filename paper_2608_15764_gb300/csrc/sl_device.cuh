@@ -282,10 +282,11 @@ __device__ __forceinline__ uint64_t& cta_start_stamp() {
 // order) into the CTA's partial a.parts[blockIdx.x], and thread 0 raises the
 // launch's end stamp to this CTA's %globaltimer.  With
 // a.result set, the last CTA to get here then runs final_combine.  `fw` is
-// this warp's index among the nfw (<= 32) folding warps.
+// this warp's index among the nfw (<= 32) folding warps; `cta_err`, if given,
+// is a CTA-local error code (shared memory) that thread 0 publishes to *a.err.
 template <int DT>
 __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint32_t fw, uint32_t nfw,
-                                           const KArgs& a) {
+                                           const KArgs& a, const uint32_t* cta_err = nullptr) {
     __shared__ WarpPartial sp[32];
     const uint32_t lane = threadIdx.x & 31;
     // A launch that may have started before the previous one finished
@@ -332,6 +333,7 @@ __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint3
             p.hi = hi;
             p.lo = lo;
             a.parts[blockIdx.x] = p;
+            if (cta_err && *cta_err) atomicCAS(a.err, 0u, *cta_err);  // before this CTA is counted done
             atomicMin(reinterpret_cast<unsigned long long*>(a.window), cta_start_stamp());
             atomicMax(reinterpret_cast<unsigned long long*>(a.window + 1), gtimer());
         }

@@ -63,8 +63,8 @@ class Point:
     @property
     def overlapped(self) -> bool:
         """Back-to-back passes run as programmatic dependent launches
-        (sl_enqueue_steps): every mechanism but TMA."""
-        return self.mech != SL_TMA
+        (sl_enqueue_steps): every mechanism and traversal."""
+        return True
 
     @property
     def offered(self) -> int:

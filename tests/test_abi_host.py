@@ -54,7 +54,6 @@ def test_argument_errors_before_any_device_use(lib):
         (lib.sl_enqueue_steps(one, 1, 16, 0, None, 2, 64), ARG),
         (lib.sl_enqueue_steps(one, 1, 16, 0, C.byref(cfg), 0, 64), ARG),
         (lib.sl_enqueue_steps(one, 0, 16, 0, C.byref(cfg), 2, 64), ARG),
-        (lib.sl_enqueue_steps(one, 1, 16, 0, C.byref(_cfg(_abi.SL_TMA)), 2, 64), ARG),
         (lib.sl_enqueue_steps(one, 1, 16, 0, C.byref(_cfg(flush_l2=1)), 2, 64), ARG),
         (lib.sl_coverage(16, 16, C.byref(cfg), None, C.byref(r)), ARG),
         (lib.sl_coverage(16, 16, C.byref(cfg), 64, None), ARG),

@@ -46,6 +46,8 @@ def _results(sl, out, n):
     ("cpasync", dict(k=4, cta=256), 16), ("ldsts", dict(k=4, cta=256), 16),
     ("ldg", dict(k=12, cta=256, order="dyn"), 16), ("ldg", dict(k=2, cta=512, order="dyn"), 16),
     ("ldg32", dict(k=6, cta=256, order="dyn"), 32),
+    ("tma", dict(cta=256, stage_bytes=16384, stages=4), 16), ("tma", dict(cta=512, stage_bytes=65536, stages=2,
+                                                                         order="desc"), 16),
 ])
 def test_steps_each_pass_matches_oracle(sl, data, mech, kw, loads):
     dev, _, want = data
@@ -138,7 +140,7 @@ def test_steps_empty_and_rejected(sl, data):
     torch.cuda.synchronize()
     for r in _results(sl, out, 3):
         assert (r.sum_u32, r.xor_u64, r.issued_loads) == (0, 0, 0)
-    for cfg, steps in [(sl.config("tma"), 2), (sl.config("ldg", flush_l2=True), 2), (sl.config("ldg"), 0)]:
+    for cfg, steps in [(sl.config("ldg", flush_l2=True), 2), (sl.config("ldg"), 0)]:
         with pytest.raises(sl.SLError) as e:
             sl.sl_enqueue_steps(dev, out, steps, dtype=sl.SL_U32, cfg=cfg)
         assert e.value.status == sl.SL_ERR_ARG
@@ -168,3 +170,22 @@ def test_dynamic_steps_float_sums(sl):
     torch.cuda.synchronize()
     for r in _results(sl, out, 6):
         assert abs(r.fsum - ref) <= 2e-6 * abs(ref)
+
+
+def test_tma_steps_report_a_timeout_on_its_own_pass(sl, data):
+    """A TMA pass whose bounded wait gives up (debug flag: one stage never
+    armed) reports SL_ERR_TIMEOUT in its own result, and the passes before and
+    after it -- overlapped with it -- are unaffected."""
+    dev, _, want = data
+    ok = sl.config("tma", cta=256, stage_bytes=16384, stages=4)
+    bad = sl.config("tma", cta=256, stage_bytes=16384, stages=4, debug_flags=sl.SL_DEBUG_TMA_SKIP_STAGE)
+    out = torch.zeros(7 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rb = sl.RESULT_BYTES
+    sl.sl_enqueue_steps(dev, out[: 3 * rb], 3, dtype=sl.SL_U32, cfg=ok)
+    sl.sl_enqueue_steps(dev, out[3 * rb: 4 * rb], 1, dtype=sl.SL_U32, cfg=bad)
+    sl.sl_enqueue_steps(dev, out[4 * rb:], 3, dtype=sl.SL_U32, cfg=ok)
+    torch.cuda.synchronize()
+    res = _results(sl, out, 7)
+    assert res[3].status == sl.SL_ERR_TIMEOUT
+    for i in (0, 1, 2, 4, 5, 6):
+        assert (res[i].sum_u32, res[i].xor_u64, res[i].status) == (*want, 0), i

@@ -69,5 +69,5 @@ def test_point_catalogue(p, nbytes):
     q = tune.parse_point(p.spec())
     assert q.label() == p.label() or p.cop  # cop is not in the dynamic/32-byte specs
     assert p.loads(nbytes) in (nbytes // 16, (nbytes + 31) // 32)
-    assert p.overlapped == (p.mech != 2)
+    assert p.overlapped
     assert p.offered > 0 and math.isfinite(p.offered)

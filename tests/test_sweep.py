@@ -117,7 +117,7 @@ def test_tune_points_specs_loads_and_choice():
     assert p.mech == SL_LDG32 and p.order == SL_DYN and p.overlapped
     assert p.cfg(grid=0).grid == 0 and p.cfg().order == SL_DYN and p.cfg(order="asc").order == 0
     assert p.loads(4096 + 16) == 129 and tune.parse_point("ldg:2:256").loads(4096 + 16) == 257
-    assert tune.parse_point("ldg:3:256").overlapped and not tune.parse_point("tma:16384:2:256").overlapped
+    assert tune.parse_point("ldg:3:256").overlapped and tune.parse_point("tma:16384:2:256").overlapped
     a, b, c = tune.parse_point("ldg:2:256"), tune.parse_point("ldg:8:256"), tune.parse_point("tma:65536:2:256")
     a.gbs, b.gbs, c.gbs = [7000.0], [7300.0], [7310.0]
     a.step_gbs, b.step_gbs, c.step_gbs = [7500.0], [7400.0], []
