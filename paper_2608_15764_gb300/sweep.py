@@ -40,9 +40,13 @@ GPU and checked against the first cell's checksum):
   c2w  the residency grid of c2 at the other two load widths: 4-byte loads
        (K in {1,2,4,8,16}) and 32-byte loads (K in {1,2,3,4,6,8}); with c2
        it gives the paper's regime map over warps x width.
-  cpskew  cp.async D in {1,2,4,8} and the matched LDG->STS kernel (G=4) with the
+  cpskew  cp.async D in {1,2,4,8} and the matched LDG->STS kernel (G=4) at 256
+       threads, and cp.async D=4 at 64/128/512/1024 threads, with the
        shared-memory ring 0, 16, 32 or 64 bytes past a 128-byte boundary
        (SL_DEBUG_SMEM_SKEW), 1 GiB: the destination alignment's effect.
+  c2fixed  the residency grid (CTA 256/512 x 1-8 resident CTAs/SM x K) under
+       the paper's fixed-iteration control: 4 GiB of loads wrapping over a
+       2 GiB allocation; regime map as for c2.
   fixedit  the paper's own fixed-iteration control (§3, §4.2): the primary
        cell shape (1,024-thread CTAs, .cg, 16 B) issuing 16,785 MiB of loads
        that wrap around a 512 MiB or 4 GiB allocation, at 132 CTAs (the
@@ -102,6 +106,16 @@ def _cells(config: str, sms: int):
             for d in (1, 2, 4, 8):
                 yield dict(mech="cpasync", k=d, cta=256, grid=0, skew=skew, gib=1)
             yield dict(mech="ldsts", k=4, cta=256, grid=0, skew=skew, gib=1)
+            for cta in (64, 128, 512, 1024):
+                yield dict(mech="cpasync", k=4, cta=cta, grid=0, skew=skew, gib=1)
+    elif config == "c2fixed":
+        # the residency grid under the paper's fixed-iteration control: 4 GiB
+        # of 16-byte loads wrapping over a 2 GiB allocation
+        target = (4 << 30) // 16
+        for cta in (256, 512):
+            for r in range(1, 9):
+                for k in (1, 2, 3, 4, 6, 8, 12, 16):
+                    yield dict(mech="ldg", k=k, cta=cta, grid=r * sms, resident_req=r, target_loads=target, gib=2)
     elif config == "fixedit":
         # paper §3 / §4.2: the primary cell under the paper's own fixed-iteration
         # control (16,785 MiB of 16-byte loads, wrapping over the allocation),
@@ -500,9 +514,11 @@ def regime_map(rows):
     order) over the K values present."""
     curves = {}
     for r in rows:
-        if r.get("config") not in ("c2", "c2w") or r.get("status") or r.get("gbs_median") is None:
+        if r.get("config") not in ("c2", "c2w", "c2fixed") or r.get("status") or r.get("gbs_median") is None:
             continue
         key = (WIDTH_BYTES[r.get("mech", "ldg")], r["cta"], r["resident_req"], r["order"])
+        if r.get("config") == "c2fixed":
+            key = ("fixed",) + key
         curves.setdefault(key, {})[r["k"]] = r["gbs_median"]
     out = {}
     for key, byk in sorted(curves.items()):
@@ -560,7 +576,7 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c2w", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
+                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
                              "cpratio", "ladder", "k1gate", "two", "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
@@ -589,7 +605,7 @@ def main(argv=None):
     if a.config == "fixedit":
         for s in fixed_mismatch(rows):
             print(json.dumps({"fixed_iteration": s}), flush=True)
-    if a.config in ("c2", "c2w"):
+    if a.config in ("c2", "c2w", "c2fixed"):
         rm = regime_map(rows)
         counts = {c: sum(1 for v in rm.values() if v == c) for c in ("saturating", "peak-decline", "rising-censored")}
         print(json.dumps({"regime_counts": counts, "curves": len(rm)}), flush=True)
