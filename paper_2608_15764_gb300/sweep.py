@@ -61,6 +61,10 @@ GPU and checked against the first cell's checksum):
   two  paper §4.4: two co-resident plain-load streams in one CTA per SM,
        stream A = 1/2/4/8/16 warps, stream B = 0..16 warps, K = 1, 2, 4;
        displacement of A's bandwidth by B.
+  ncu-primary  the primary cell shape (1,024 threads, one CTA per SM), K in
+       {1,2,4,8}, 1 GiB, one launch each: the paper's counter audit per K.
+  ncu-alloc  LDG K = 2 and 8 (256 threads, 4 x SMs) on 512 MiB ... 20 GiB, one
+       launch each: counters per allocation size (one-pass metrics only).
   ncu-points  every candidate point of the benchmark (tune.default_points)
        on 1 GiB, then LDG K=2 and K=8 on 512 MiB and 2 GiB (one launch each,
        no warm-up): DRAM bytes per launch for the roofline, and the paper's
@@ -184,6 +188,17 @@ def _cells(config: str, sms: int):
                 yield dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop,
                            trav=p.order, gib=1)
         for gib in (0.5, 2):
+            for k in (2, 8):
+                yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
+    elif config == "ncu-primary":
+        # the paper's primary cell shape (one 1,024-thread CTA per SM) on 1 GiB:
+        # its counter audit (§4.2) per K
+        for k in (1, 2, 4, 8):
+            yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=1)
+    elif config == "ncu-alloc":
+        # the allocation sweep's sizes at K = 2 and 8 (one launch each): DRAM
+        # bytes, L1->L2 sectors and L2 hit rate per size
+        for gib in (0.5, 1, 2, 4, 8, 16, 20):
             for k in (2, 8):
                 yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
     elif config == "ncu":
@@ -576,7 +591,7 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "l2",
+                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "ncu-primary", "ncu-alloc", "l2",
                              "cpratio", "ladder", "k1gate", "two", "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
