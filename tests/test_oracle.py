@@ -4,7 +4,6 @@ casts and the paper's printed fixed-work figures.  CPU only."""
 import json
 import math
 import os
-import struct
 
 import numpy as np
 import pytest
