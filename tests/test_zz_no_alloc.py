@@ -12,6 +12,7 @@ every other test; it also passes on its own in a fresh process."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2608_15764_gb300 import workloads as wl
 
 torch = pytest.importorskip("torch")
@@ -40,6 +41,7 @@ def _noalloc(sl, buf, dtype, cfg, nbytes=None):
 def test_noalloc_matches_sl_run_two_calls(sl):
     dev = torch.empty(NBYTES, dtype=torch.uint8, device="cuda")
     sl.sl_fill_splitmix64(dev, seed=1)
+    exact = oracle.checksum(wl.splitmix_u32(1, NBYTES // 4))
     # two calls in a row with different launch shapes: the second must not
     # see anything of the first call's scratch contents
     for cfg in [sl.config("ldg", k=4, cta=256), sl.config("ldg", k=2, cta=512, grid=37, order="desc")]:
@@ -47,17 +49,20 @@ def test_noalloc_matches_sl_run_two_calls(sl):
         got = _noalloc(sl, dev, sl.SL_U32, cfg)
         assert got.status == 0
         assert (got.sum_u32, got.xor_u64, got.issued_loads) == (want.sum_u32, want.xor_u64, want.issued_loads)
+        assert (got.sum_u32, got.xor_u64) == exact  # and both match the oracle
 
 
 @pytest.mark.parametrize("dtype", [wl.F32, wl.BF16, wl.FP8_E4M3])
 def test_noalloc_float_two_calls(sl, dtype):
     host = wl.payload(dtype, NBYTES // wl.ELEM_BYTES[dtype])
     dev = torch.from_numpy(host.view(np.uint8)).cuda()
-    for cfg in [sl.config("ldg", k=8, cta=128), sl.config("ldg", k=1, cta=256, passes=2)]:
+    exact, _ = oracle.fsum(dtype, host)
+    for cfg, passes in [(sl.config("ldg", k=8, cta=128), 1), (sl.config("ldg", k=1, cta=256, passes=2), 2)]:
         want = sl.sl_run(dev, dtype=dtype, cfg=cfg)
         got = _noalloc(sl, dev, dtype, cfg)
         assert (got.sum_u32, got.xor_u64, got.issued_loads) == (want.sum_u32, want.xor_u64, want.issued_loads)
         assert abs(got.fsum - want.fsum) <= TOL * abs(want.fsum)
+        assert abs(got.fsum - passes * exact) <= TOL * abs(passes * exact)  # and against the oracle
 
 
 def test_noalloc_limits_and_empty(sl):
