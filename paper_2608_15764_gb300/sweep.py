@@ -49,9 +49,12 @@ GPU and checked against the first cell's checksum):
        2 GiB allocation; regime map as for c2.
   fixedit  the paper's own fixed-iteration control (§3, §4.2): the primary
        cell shape (1,024-thread CTAs, .cg, 16 B) issuing 16,785 MiB of loads
-       that wrap around a 512 MiB or 4 GiB allocation, at 132 CTAs (the
-       paper's H100) and one CTA per GB300 SM, K in {1,2,4,8}; reports the
-       issued counts (mismatch across K) and GB/s of the issued bytes.
+       that wrap around a 512 MiB, 2, 4, 8 or 20 GiB allocation, at 132 CTAs
+       (the paper's H100) and one CTA per GB300 SM, K in {1,2,4,8}; reports
+       the issued counts (mismatch across K) and GB/s of the issued bytes.
+  ncu-fixed / ncu-fixed-large  one launch per cell of the fixed-iteration
+       control at 132 CTAs, K = 2 and 8, on 512 MiB and 2 GiB (any metrics) or
+       8 and 20 GiB (one-pass metrics only).
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
@@ -125,10 +128,17 @@ def _cells(config: str, sms: int):
         # control (16,785 MiB of 16-byte loads, wrapping over the allocation),
         # at the paper's 132 CTAs and at GB300's SM count
         target = 16785 * (1 << 20) // 16
-        for gib in (0.5, 4):
+        for gib in (0.5, 2, 4, 8, 20):
             for grid in (132, sms):
                 for k in (1, 2, 4, 8):
                     yield dict(mech="ldg", k=k, cta=1024, grid=grid, target_loads=target, gib=gib)
+    elif config in ("ncu-fixed", "ncu-fixed-large"):
+        # counters of the fixed-iteration control at K = 2 and 8, 132 CTAs:
+        # small allocations (all metrics) or large ones (one-pass metrics)
+        target = 16785 * (1 << 20) // 16
+        for gib in ((0.5, 2) if config == "ncu-fixed" else (8, 20)):
+            for k in (2, 8):
+                yield dict(mech="ldg", k=k, cta=1024, grid=132, target_loads=target, gib=gib)
     elif config == "c2w":
         for cta in (128, 256, 512):
             for r in range(1, 9):
@@ -591,7 +601,7 @@ def summarize(rows):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "ncu-primary", "ncu-alloc", "l2",
+                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "ncu-primary", "ncu-alloc", "ncu-fixed", "ncu-fixed-large", "l2",
                              "cpratio", "ladder", "k1gate", "two", "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
