@@ -109,7 +109,8 @@ typedef struct sl_config {
     int32_t stages;      /* SL_TMA: ring depth, 2..8 */
     int32_t cta;         /* threads per CTA that fold loads, a multiple of 32:
                             32..1024 for LDG/CPASYNC (LDG with K > 8: up to 512);
-                            32..992 for TMA, which adds one producer warp. */
+                            TMA: 32..992 with SL_RING_CTA, which adds one
+                            producer warp; 32..1024 with SL_RING_WARP. */
     int32_t grid;        /* CTAs; <= 0 selects min(4, resident CTAs per SM) x SMs */
     int32_t order;       /* sl_order: traversal of the tiles; never changes the
                             integer result */
@@ -126,6 +127,8 @@ typedef struct sl_config {
                             host buffer directly over the CPU-GPU link (pinned
                             memory, or pageable memory where the device can
                             address it), with no staging copies */
+    int32_t tma_ring;    /* SL_TMA only: sl_tma_ring, how the stages are shared */
+    int32_t reserved;    /* 0 */
     uint64_t target_loads; /* 0 (default): exact fixed work, every vector read
                             once per pass.  > 0: the paper's fixed-iteration
                             control (§3 "Fixed-work control"): every thread runs
@@ -138,6 +141,22 @@ typedef struct sl_config {
                             tile (SL_ERR_ARG otherwise). */
     void*   stream;      /* cudaStream_t to launch on; NULL = legacy default stream */
 } sl_config;
+
+/* Layout of the TMA rings (SL_TMA).
+ *   SL_RING_CTA:  one ring of `stages` stages of stage_bytes per CTA, filled by
+ *                 a dedicated producer warp (one elected lane issues every bulk
+ *                 copy) and read by all cta/32 consumer warps together: each
+ *                 stage costs every consumer warp one full-barrier wait and one
+ *                 empty-barrier arrive.  Dynamic shared memory stages *
+ *                 stage_bytes.
+ *   SL_RING_WARP: every warp owns a ring of `stages` stages of stage_bytes,
+ *                 filled by its own lane 0 and read by its own 32 lanes only,
+ *                 so a stage costs one wait per warp and no cross-warp
+ *                 synchronisation (small stages no longer pay a CTA-wide
+ *                 protocol per 16 bytes a thread reads).  Chunks are dealt to
+ *                 warps grid-wide.  Dynamic shared memory (cta/32) * stages *
+ *                 (stage_bytes + 8). */
+typedef enum { SL_RING_CTA = 0, SL_RING_WARP = 1 } sl_tma_ring;
 
 #define SL_DEBUG_TMA_SKIP_STAGE 1
 /* Experiment knob for SL_CPASYNC and SL_LDSTS: place the shared-memory ring n
@@ -224,9 +243,9 @@ int sl_plan(uint64_t bytes, int32_t dtype, const sl_config* cfg, sl_result* out)
  * guarded so that issued loads = passes*bytes/16 exactly at every K.  TMA
  * walks stage-sized chunks the same way.  dtype selects the fold: SL_U32
  * computes sum_u32 / xor_u64; float dtypes also compute fsum (per-thread
- * compensated FP32 sum -- FP32: every element, BF16/FP8: per-vector sums --
- * with each addition's error recovered by TwoSum, double-float merges of
- * warps and CTAs, FP64 combine of per-CTA partials).  Synchronous: returns
+ * compensated FP32 sum -- FP32 and BF16: every element; FP8: the two exact
+ * sums of each half vector -- with each addition's error recovered by TwoSum,
+ * double-float merges of warps and CTAs, FP64 combine of per-CTA partials).  Synchronous: returns
  * after the result is on the host. */
 int sl_run(const void* dev_buf, uint64_t bytes, int32_t dtype, const sl_config* cfg,
            sl_result* out);
@@ -318,7 +337,7 @@ int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t war
  * vectors q+1).  Instantiations exist for: SL_LDG K 1/3/8/16 grid-stride and
  * K 2/12 SL_DYN at cta 128/256/512 (SL_COP_CG); SL_LDG32 K 1/3/8 at cta 256
  * (grid-stride or SL_DYN); the fixed-iteration control at K 2/8, cta 256/1024;
- * SL_CPASYNC D 1/4/16; SL_LDSTS G 1/16; SL_TMA (any ring) -- SL_ERR_ARG
+ * SL_CPASYNC D 1/4/16; SL_LDSTS G 1/16; SL_TMA (either ring layout) -- SL_ERR_ARG
  * otherwise.  A debug tool (the counting atomics slow the kernel); no paper
  * counterpart. */
 int sl_coverage(const void* dev_buf, uint64_t bytes, const sl_config* cfg, uint32_t* dev_counts, sl_result* out);
@@ -371,8 +390,9 @@ typedef struct sl_batch_desc {
  * max_bytes (and dtype == dtype, or dtype == -1 for any) run with cfg.  In
  * cfg: mech, k (LDG K in {1,2,3,4,6,8,12,16}, cp.async D 1..8), stage_bytes,
  * stages, cta (LDG: 128/256/512) and grid (<= 0: resident CTAs per SM x
- * SMs, a persistent grid) are used; order, passes, flush_l2, cop,
- * debug_flags and stream are ignored. */
+ * SMs, a persistent grid) are used (TMA classes run one ring per CTA:
+ * tma_ring must be SL_RING_CTA); order, passes, flush_l2, cop, debug_flags
+ * and stream are ignored. */
 typedef struct sl_tune_entry {
     uint64_t  min_bytes;
     uint64_t  max_bytes;

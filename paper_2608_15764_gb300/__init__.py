@@ -20,7 +20,7 @@ from ._abi import (  # noqa: F401  (re-exported constants)
     SL_ASC, SL_BF16, SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256, SL_CPASYNC,
     SL_DEBUG_SMEM_SKEW, SL_DEBUG_TMA_SKIP_STAGE, SL_DESC, SL_DYN, SL_ERR_ALIGN, SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_INFEASIBLE,
     SL_ERR_NODEV, SL_ERR_OOM, SL_ERR_TIMEOUT, SL_F32, SL_FP8_E4M3, SL_LDG, SL_LDG4, SL_LDG32, SL_LDSTS, SL_MAX_D, SL_MAX_K,
-    SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_TMA, SL_U32,
+    SL_MAX_STAGES, SL_MIN_STAGES, SL_NOALLOC_MAX_CTAS, SL_OK, SL_RING_CTA, SL_RING_WARP, SL_TMA, SL_U32,
     STATUS_NAMES, RESULT_BYTES, load, sl_batch_desc, sl_chase_result, sl_config, sl_devinfo, sl_result,
     sl_tune_entry, sl_twostream_result,
 )
@@ -28,6 +28,7 @@ from ._abi import (  # noqa: F401  (re-exported constants)
 MECHS = {"ldg": SL_LDG, "cpasync": SL_CPASYNC, "tma": SL_TMA, "ldsts": SL_LDSTS, "ldg4": SL_LDG4, "ldg32": SL_LDG32}
 DTYPES = {"u32": SL_U32, "f32": SL_F32, "bf16": SL_BF16, "fp8": SL_FP8_E4M3}
 ORDERS = {"asc": SL_ASC, "desc": SL_DESC, "dyn": SL_DYN}
+RINGS = {"cta": SL_RING_CTA, "warp": SL_RING_WARP}
 
 
 class SLError(RuntimeError):
@@ -80,9 +81,11 @@ def _stream_handle(stream):
 
 def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *, stage_bytes: int = 16384,
            stages: int = 4, flush_l2: bool = False, passes: int = 1, cop: int = SL_COP_CG,
-           debug_flags: int = 0, host_direct: bool = False, target_loads: int = 0, stream=None) -> sl_config:
+           debug_flags: int = 0, host_direct: bool = False, target_loads: int = 0, ring="cta",
+           stream=None) -> sl_config:
     """Build an sl_config.  mech: "ldg" / "cpasync" / "tma" (or the enum);
-    k: K for LDG, depth D for cp.async; stage_bytes/stages for TMA."""
+    k: K for LDG, depth D for cp.async; stage_bytes/stages/ring ("cta": one
+    ring per CTA, "warp": one ring per warp) for TMA."""
     c = sl_config()
     c.mech = MECHS[mech] if isinstance(mech, str) else int(mech)
     c.k = int(k)
@@ -97,6 +100,7 @@ def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *
     c.debug_flags = int(debug_flags)
     c.host_direct = int(bool(host_direct))
     c.target_loads = int(target_loads)
+    c.tma_ring = RINGS[ring] if isinstance(ring, str) else int(ring)
     c.stream = _stream_handle(stream)
     return c
 

@@ -30,6 +30,7 @@ SL_LDG, SL_CPASYNC, SL_TMA, SL_LDSTS, SL_LDG4, SL_LDG32 = 0, 1, 2, 3, 4, 5
 SL_ASC, SL_DESC, SL_DYN = 0, 1, 2
 SL_COP_CG, SL_COP_CG_L2_256, SL_COP_NC_NA_L2_256 = 0, 1, 2
 SL_MAX_K, SL_MAX_D, SL_MIN_STAGES, SL_MAX_STAGES = 16, 16, 2, 8
+SL_RING_CTA, SL_RING_WARP = 0, 1
 SL_DEBUG_TMA_SKIP_STAGE = 1
 SL_DEBUG_SMEM_SKEW_SHIFT = 8
 
@@ -52,6 +53,8 @@ class sl_config(ctypes.Structure):
         ("cop", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
         ("host_direct", ctypes.c_int32),
+        ("tma_ring", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("target_loads", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
     ]
@@ -129,8 +132,8 @@ class sl_tune_entry(ctypes.Structure):
 
 
 assert ctypes.sizeof(sl_batch_desc) == 24
-assert ctypes.sizeof(sl_tune_entry) == 88
-assert ctypes.sizeof(sl_config) == 64
+assert ctypes.sizeof(sl_tune_entry) == 96
+assert ctypes.sizeof(sl_config) == 72
 assert ctypes.sizeof(sl_result) == 72
 RESULT_BYTES = ctypes.sizeof(sl_result)
 

@@ -311,10 +311,20 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
             return fail(SL_ERR_INFEASIBLE, "TMA stage size %d not 4096/16384/65536", cfg->stage_bytes);
         if (cfg->stages < SL_MIN_STAGES || cfg->stages > SL_MAX_STAGES)
             return fail(SL_ERR_ARG, "TMA stages %d not in %d..%d", cfg->stages, SL_MIN_STAGES, SL_MAX_STAGES);
-        if (cta > 992) return fail(SL_ERR_ARG, "TMA consumer threads %d > 992", cta);
-        p->fn = sl::tma_kernel(dtype);
-        p->block = cta + 32;
-        p->smem = static_cast<size_t>(cfg->stages) * cfg->stage_bytes;
+        if (cfg->tma_ring == SL_RING_WARP) {
+            // one ring per warp, filled by the warp's own lane 0; its full
+            // barriers follow the rings in dynamic shared memory
+            p->fn = sl::tma_warp_kernel(dtype);
+            p->block = cta;
+            p->smem = static_cast<size_t>(cta / 32) * cfg->stages * (static_cast<size_t>(cfg->stage_bytes) + 8);
+        } else if (cfg->tma_ring == SL_RING_CTA) {
+            if (cta > 992) return fail(SL_ERR_ARG, "TMA consumer threads %d > 992", cta);
+            p->fn = sl::tma_kernel(dtype);
+            p->block = cta + 32;
+            p->smem = static_cast<size_t>(cfg->stages) * cfg->stage_bytes;
+        } else {
+            return fail(SL_ERR_ARG, "bad tma_ring %d", cfg->tma_ring);
+        }
         tile_vec = static_cast<uint64_t>(cfg->stage_bytes) / 16;
         p->warps = cta / 32;
         break;
@@ -426,7 +436,7 @@ const void* coverage_fn(const sl_config* cfg) {
     case SL_LDG32: return sl::ldg32_cov_kernel(cfg->k, cfg->cta, dyn);
     case SL_CPASYNC: return sl::cpasync_cov_kernel(cfg->k);
     case SL_LDSTS: return sl::ldsts_cov_kernel(cfg->k);
-    case SL_TMA: return sl::tma_cov_kernel();
+    case SL_TMA: return cfg->tma_ring == SL_RING_WARP ? sl::tma_warp_cov_kernel() : sl::tma_cov_kernel();
     default: return nullptr;
     }
 }

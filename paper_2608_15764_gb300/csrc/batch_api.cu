@@ -128,6 +128,9 @@ int plan_group(Group& g, int sms, int smem_optin) {
             return bfail(SL_ERR_INFEASIBLE, "tuning entry: TMA stage size not 4096/16384/65536");
         if (c.stages < SL_MIN_STAGES || c.stages > SL_MAX_STAGES) return bfail(SL_ERR_ARG, "tuning entry: TMA stages");
         if (c.cta > 992) return bfail(SL_ERR_ARG, "tuning entry: TMA consumer threads > 992");
+        if (c.tma_ring != SL_RING_CTA)
+            return bfail(SL_ERR_ARG, "tuning entry: the batched TMA class kernel has one ring per CTA "
+                         "(tma_ring must be SL_RING_CTA)");
         g.fn = sl::batch_tma_kernel(g.dtype);
         g.block = c.cta + 32;
         g.smem = static_cast<size_t>(c.stages) * c.stage_bytes;

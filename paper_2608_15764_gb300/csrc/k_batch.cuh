@@ -51,7 +51,8 @@ template <int DT>
 __device__ __forceinline__ void warp_item_store(const Acc<DT>& acc, WarpPartial* dst) {
     uint32_t s = acc.s;
     uint64_t x = (static_cast<uint64_t>(acc.xh) << 32) | acc.xl, n = acc.n;
-    float hi = acc.fs, lo = acc.fe;
+    float hi = 0.0f, lo = 0.0f;
+    if constexpr (DT != SL_U32) acc.float_part(hi, lo);
     warp_merge<DT>(s, x, n, hi, lo);
     if ((threadIdx.x & 31) == 0) {
         WarpPartial p;

@@ -1,8 +1,9 @@
-// k_tma.cu -- the TMA (bulk asynchronous copy) streaming kernel.
+// k_tma.cu -- the TMA (bulk asynchronous copy) streaming kernels.
 //
 // The paper names Hopper's TMA and bulk-asynchronous copies (§2) but has no
-// TMA kernel; this ring is the library's own Blackwell design.
+// TMA kernel; both ring layouts below are the library's own Blackwell design.
 //
+// ---- k_tma: one ring per CTA (SL_RING_CTA) ----
 // CTA = one producer warp + `cta` consumer threads.  The buffer is cut into
 // stage-sized chunks (stage_bytes, the last one ragged); CTA b takes chunks
 // b, b+grid, ... over all passes (reversed for SL_DESC).  Lane 0 of warp 0
@@ -31,7 +32,7 @@
 namespace sl {
 
 template <int DT, bool COV = false>
-__global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
+__global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ __align__(8) uint64_t full[SL_MAX_STAGES];
     __shared__ __align__(8) uint64_t empty[SL_MAX_STAGES];
@@ -122,7 +123,151 @@ __global__ void __launch_bounds__(1024) k_tma(const KArgs a) {
     cta_finish<DT>(acc, warp != 0, warp - 1, ncw, a, &cta_err);
 }
 
+// ---- k_tma_warp: one ring per warp (SL_RING_WARP) ----
+// Every warp owns a ring of nst stages of stage_bytes in dynamic shared memory
+// (warp w's ring after those of warps 0..w-1, then the CTA's full barriers,
+// one per stage per warp, count 1).  Its lane 0 is the ring's only producer
+// and its 32 lanes the only consumers, so a stage needs no empty barrier:
+// once the warp has read stage s (__syncwarp), lane 0 re-arms it with
+// arrive.expect_tx and issues the next cp.async.bulk into it.
+//
+// Chunks (stage-sized pieces of the buffer, the last one ragged) are dealt to
+// warps grid-wide: global warp g = blockIdx.x * W + w (W warps per CTA) takes
+// chunks g, g + G, g + 2G, ... over all passes (G = grid * W; chunk c reads
+// piece c mod nchunks, counted from the last piece for SL_DESC).  A warp's
+// j-th chunk lives in stage j mod nst and has landed when that stage's
+// barrier completes phase j / nst; the producer refills a stage only after
+// its warp has read it, so no barrier runs more than one phase ahead of its
+// waiter.  A full stage gives each lane stage_bytes/512 vectors (8 for 4 KiB),
+// read 8 at a time.
+//
+// Waits are bounded as in k_tma: a timed-out wait records the error in the
+// CTA's error word, raises the abort flag (other warps stop at their next
+// wait) and the warp leaves its loop with all lanes together; lane 0 then
+// waits (bounded) for every copy it issued to land before the CTA exits.
+template <int DT, bool COV = false>
+__global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
+    extern __shared__ __align__(128) uint8_t ring[];
+    __shared__ volatile int abort_flag;
+    __shared__ uint32_t cta_err;
+
+    cta_start(a);
+    const uint32_t nst = static_cast<uint32_t>(a.nst);
+    const uint64_t nchunks = a.ntiles;
+    const uint64_t total = a.total;
+    const uint32_t stage_bytes = a.tile_vec * 16u;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const uint64_t bytes = a.nvec * 16ull;
+    const uint8_t* __restrict__ gbuf = static_cast<const uint8_t*>(a.buf);
+    const uint32_t my_ring = smem_addr(ring) + warp * nst * stage_bytes;
+    const uint32_t my_full = smem_addr(ring) + nw * nst * stage_bytes + warp * nst * 8u;
+    const uint64_t G = static_cast<uint64_t>(gridDim.x) * nw;
+    const uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * nw + warp;
+    const bool skip_one = (a.debug & SL_DEBUG_TMA_SKIP_STAGE) && g0 == 0;  // debug: leave chunk 1 of warp 0 unarmed
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        cta_err = 0;
+    }
+    if (lane == 0) {
+        for (uint32_t s = 0; s < nst; ++s) mbar_init(my_full + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    // byte offset and length of chunk c
+    const auto piece = [&](uint64_t c, uint64_t& off, uint32_t& len) {
+        uint64_t t = c < nchunks ? c : c % nchunks;
+        if (a.desc) t = nchunks - 1 - t;
+        off = t * stage_bytes;
+        const uint64_t left = bytes - off;
+        len = left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes;
+    };
+    uint32_t armed = 0;     // lane 0: bit s = stage s has had a copy issued
+    uint32_t last_par = 0;  // lane 0: bit s = parity of the phase of stage s's last copy
+    const auto issue = [&](uint32_t s, uint32_t par, uint64_t c) {
+        uint64_t off;
+        uint32_t len;
+        piece(c, off, len);
+        mbar_arrive_expect_tx(my_full + 8 * s, len);
+        bulk_g2s(my_ring + s * stage_bytes, gbuf + off, len, my_full + 8 * s);
+        if constexpr (COV) {
+            for (uint64_t v = off >> 4; v < (off + len) >> 4; ++v) cov_count<COV>(a, v);
+        }
+        armed |= 1u << s;
+        last_par = (last_par & ~(1u << s)) | (par << s);
+    };
+    if (lane == 0) {
+        for (uint32_t j = 0; j < nst; ++j) {
+            const uint64_t c = g0 + j * G;
+            if (c >= total) break;
+            if (skip_one && j == 1) continue;
+            issue(j, 0u, c);
+        }
+    }
+
+    Acc<DT> acc;
+    uint32_t s = 0, r = 0;  // stage and round of the warp's current chunk (its j-th: j = r*nst + s)
+#pragma unroll 1
+    for (uint64_t c = g0; c < total; c += G) {
+        const bool got = bounded_wait(my_full + 8 * s, r & 1u, &cta_err, a.timeout_ns, &abort_flag, true,
+                                      DEV_ERR_TIMEOUT_FULL);
+        if (!__all_sync(FULL_MASK, got)) break;  // warp-uniform exit
+        uint64_t off;
+        uint32_t len;
+        piece(c, off, len);
+        const uint32_t base = my_ring + s * stage_bytes + 16u * lane;
+        if (len == stage_bytes) {
+            const uint32_t per_lane = stage_bytes >> 9;  // a multiple of 8
+#pragma unroll 1
+            for (uint32_t i = 0; i < per_lane; i += 8) {
+                uint4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = lds16(base + 512u * (i + u));
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc.fold(v[u]);
+            }
+            acc.n += per_lane;
+        } else {
+            const uint32_t nv = len >> 4;
+#pragma unroll 1
+            for (uint32_t v = lane; v < nv; v += 32) {
+                acc.fold(lds16(my_ring + s * stage_bytes + 16u * v));
+                acc.n += 1;
+            }
+        }
+        __syncwarp();  // every lane has read stage s
+        if (lane == 0) {
+            const uint64_t cn = c + nst * G;
+            if (cn < total) issue(s, (r + 1) & 1u, cn);
+        }
+        if (++s == nst) { s = 0; ++r; }
+    }
+    // Drain: every copy this warp issued must have landed before the CTA
+    // exits (immediate in normal operation; bounded after an abort).
+    if (lane == 0) {
+        for (uint32_t t = 0; t < nst; ++t)
+            if (armed & (1u << t))
+                bounded_wait(my_full + 8 * t, (last_par >> t) & 1u, &cta_err, a.timeout_ns, &abort_flag, false,
+                             DEV_ERR_TIMEOUT_DRAIN);
+    }
+    __syncwarp();
+    cta_finish<DT>(acc, true, warp, nw, a, &cta_err);
+}
+
 const void* tma_cov_kernel() { return reinterpret_cast<const void*>(&k_tma<SL_U32, true>); }
+const void* tma_warp_cov_kernel() { return reinterpret_cast<const void*>(&k_tma_warp<SL_U32, true>); }
+
+const void* tma_warp_kernel(int dtype) {
+    switch (dtype) {
+    case SL_U32: return reinterpret_cast<const void*>(&k_tma_warp<SL_U32>);
+    case SL_F32: return reinterpret_cast<const void*>(&k_tma_warp<SL_F32>);
+    case SL_BF16: return reinterpret_cast<const void*>(&k_tma_warp<SL_BF16>);
+    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&k_tma_warp<SL_FP8_E4M3>);
+    default: return nullptr;
+    }
+}
 
 const void* tma_kernel(int dtype) {
     switch (dtype) {

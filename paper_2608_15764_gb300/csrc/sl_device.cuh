@@ -48,40 +48,36 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// ---- per-vector float sums -------------------------------------------------
-// float32: 4 values, pairwise.
-__device__ __forceinline__ float vec_sum_f32(const uint4& v) {
-    return (__uint_as_float(v.x) + __uint_as_float(v.y)) +
-           (__uint_as_float(v.z) + __uint_as_float(v.w));
+// ---- packed float pairs -------------------------------------------------------
+// Two FP32 values in one 64-bit register pair (lane 0 = low word), operated on
+// by the sm_100-family packed instructions add/sub.rn.f32x2: each lane is an
+// ordinary IEEE round-to-nearest FP32 operation (subnormals kept), two lanes
+// per instruction.
+__device__ __forceinline__ uint64_t f2_pack(uint32_t lo_bits, uint32_t hi_bits) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo_bits), "r"(hi_bits));
+    return d;
+}
+__device__ __forceinline__ float f2_lane0(uint64_t p) { return __uint_as_float(static_cast<uint32_t>(p)); }
+__device__ __forceinline__ float f2_lane1(uint64_t p) { return __uint_as_float(static_cast<uint32_t>(p >> 32)); }
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
-// bfloat16: 8 values.  add.f32.bf16 widens its bf16 operand exactly and rounds
-// once in FP32, so each step is one FP32 addition of the decoded value.
-__device__ __forceinline__ float vec_sum_bf16(const uint4& v) {
-    float a = __uint_as_float(v.y & 0xFFFF0000u);  // high half of word 1
-    float b = __uint_as_float(v.w & 0xFFFF0000u);  // high half of word 3
-    asm("{\n\t.reg .b16 l0, h0, l1, h1;\n\t"
-        "mov.b32 {l0, h0}, %1;\n\t"
-        "mov.b32 {l1, h1}, %2;\n\t"
-        "add.rn.f32.bf16 %0, l0, %0;\n\t"
-        "add.rn.f32.bf16 %0, h0, %0;\n\t"
-        "add.rn.f32.bf16 %0, l1, %0;\n\t}"
-        : "+f"(a) : "r"(v.x), "r"(v.y));
-    asm("{\n\t.reg .b16 l0, h0, l1, h1;\n\t"
-        "mov.b32 {l0, h0}, %1;\n\t"
-        "mov.b32 {l1, h1}, %2;\n\t"
-        "add.rn.f32.bf16 %0, l0, %0;\n\t"
-        "add.rn.f32.bf16 %0, h0, %0;\n\t"
-        "add.rn.f32.bf16 %0, l1, %0;\n\t}"
-        : "+f"(b) : "r"(v.z), "r"(v.w));
-    return a + b;
-}
-
-// FP8 E4M3: 16 values.  cvt.rn.f16x2.e4m3x2 widens two codes to half exactly
-// (every E4M3 value is a half), add.f32.f16 adds a half to an FP32
-// accumulator.  Every E4M3 value is an integer multiple of 2^-9 below 2^9, so
-// any partial sum of 16 of them is a multiple of 2^-9 below 2^13 and fits the
-// 24-bit FP32 significand: the per-vector sum is exact in any order.
+// ---- per-vector FP8 sum ----------------------------------------------------------
+// FP8 E4M3: 8 values per half vector.  cvt.rn.f16x2.e4m3x2 widens two codes to
+// half exactly (every E4M3 value is a half), add.f32.f16 adds a half to an
+// FP32 accumulator.  Every E4M3 value is an integer multiple of 2^-9 below
+// 2^9, so any partial sum of 16 of them is a multiple of 2^-9 below 2^13 and
+// fits the 24-bit FP32 significand: each half's sum, and their total, are
+// exact in any order.
 __device__ __forceinline__ float fp8_word_sum(uint32_t w, float acc) {
     asm("{\n\t.reg .b16 q0, q1, a0, a1, b0, b1;\n\t.reg .b32 h0, h1;\n\t"
         "mov.b32 {q0, q1}, %1;\n\t"
@@ -97,19 +93,6 @@ __device__ __forceinline__ float fp8_word_sum(uint32_t w, float acc) {
     return acc;
 }
 
-__device__ __forceinline__ float vec_sum_fp8(const uint4& v) {
-    float a = fp8_word_sum(v.y, fp8_word_sum(v.x, 0.0f));
-    float b = fp8_word_sum(v.w, fp8_word_sum(v.z, 0.0f));
-    return a + b;
-}
-
-template <int DT>
-__device__ __forceinline__ float vec_sum(const uint4& v) {
-    if constexpr (DT == SL_F32) return vec_sum_f32(v);
-    else if constexpr (DT == SL_BF16) return vec_sum_bf16(v);
-    else return vec_sum_fp8(v);
-}
-
 // ---- coverage audit ------------------------------------------------------------
 // In the coverage instantiations (COV = true) every load of 16-byte vector i
 // also adds 1 to a.cov[i]; elsewhere this compiles to nothing.
@@ -120,24 +103,34 @@ __device__ __forceinline__ void cov_count(const KArgs& a, uint64_t i) {
 
 // ---- the fold ----------------------------------------------------------------
 // Per-thread accumulator.  Integer part (every dtype): wraparound uint32 sum
-// of the four words and XOR of the two little-endian uint64 halves.  Float
-// part: compensated FP32 summation in which every addition's rounding error
-// is recovered exactly with TwoSum and added to a separate error sum; the
-// represented value is fs + fe (error of order u^2 times sum|x| rather than
-// the 2u sum|x| of Kahan's recurrence).  FP32 payloads feed every element;
-// BF16 and FP8 payloads feed per-vector sums (exact for FP8, see
-// vec_sum_fp8; for BF16 exact unless the eight values span more than 16
-// binades).
+// of the four words and XOR of the two little-endian uint64 halves.
+//
+// Float part: compensated FP32 summation in which every addition's rounding
+// error is recovered exactly with TwoSum (Knuth) and added to a separate
+// error sum, so the represented value is s + e with an error of order u^2
+// times sum|x| (u = 2^-24) instead of the 2u sum|x| of Kahan's recurrence.
+// It runs as two independent lanes of packed f32x2 arithmetic (lane 0 takes
+// the even-numbered values of a vector, lane 1 the odd-numbered ones), so one
+// TwoSum instruction sequence serves two elements:
+//   FP32: each of the 4 values goes through TwoSum (2 packed steps);
+//   BF16: each of the 8 values is widened exactly to FP32 (a shift or a mask)
+//         and goes through TwoSum (4 packed steps), so no addition inside a
+//         vector is left uncompensated, whatever the values' range;
+//   FP8:  the two half-vector sums, each exact (fp8_word_sum), go through one
+//         packed TwoSum step.
 template <int DT>
 struct Acc {
     uint32_t s = 0, xl = 0, xh = 0;
     uint32_t n = 0;  // 16-byte loads folded by this thread (the host keeps it below 2^32)
-    float fs = 0.0f, fe = 0.0f;
+    uint64_t fs = 0, fe = 0;  // packed (lane 0, lane 1) running sums and error sums; 0 bits = +0.0f
 
-    __device__ __forceinline__ void add(float x) {
-        const float t = fs + x;
-        const float bp = t - fs;
-        fe += (fs - (t - bp)) + (x - bp);  // exact rounding error of fs + x (Knuth's TwoSum)
+    // TwoSum of the packed pair x into (fs, fe), lane by lane.
+    __device__ __forceinline__ void add2(uint64_t x) {
+        const uint64_t t = f2_add(fs, x);
+        const uint64_t bp = f2_sub(t, fs);
+        const uint64_t d1 = f2_sub(fs, f2_sub(t, bp));
+        const uint64_t d2 = f2_sub(x, bp);
+        fe = f2_add(fe, f2_add(d1, d2));
         fs = t;
     }
 
@@ -146,14 +139,25 @@ struct Acc {
         xl ^= v.x ^ v.z;
         xh ^= v.y ^ v.w;
         if constexpr (DT == SL_F32) {
-            add(__uint_as_float(v.x));
-            add(__uint_as_float(v.y));
-            add(__uint_as_float(v.z));
-            add(__uint_as_float(v.w));
-        } else if constexpr (DT != SL_U32) {
-            add(vec_sum<DT>(v));
+            add2(f2_pack(v.x, v.y));
+            add2(f2_pack(v.z, v.w));
+        } else if constexpr (DT == SL_BF16) {
+            // element 2i is the low half of word i, element 2i+1 the high half;
+            // a bfloat16 is the top 16 bits of the FP32 with the same value
+            add2(f2_pack(v.x << 16, v.x & 0xFFFF0000u));
+            add2(f2_pack(v.y << 16, v.y & 0xFFFF0000u));
+            add2(f2_pack(v.z << 16, v.z & 0xFFFF0000u));
+            add2(f2_pack(v.w << 16, v.w & 0xFFFF0000u));
+        } else if constexpr (DT == SL_FP8_E4M3) {
+            const float a = fp8_word_sum(v.y, fp8_word_sum(v.x, 0.0f));
+            const float b = fp8_word_sum(v.w, fp8_word_sum(v.z, 0.0f));
+            add2(f2_pack(__float_as_uint(a), __float_as_uint(b)));
         }
     }
+
+    // The float part as one double-float pair (hi, lo): the two lanes merged
+    // with TwoSum and renormalised.
+    __device__ __forceinline__ void float_part(float& hi, float& lo) const;
 };
 
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
@@ -170,6 +174,13 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float ohi, float ol
     se += lo + olo;
     hi = sh + se;
     lo = se - (hi - sh);
+}
+
+template <int DT>
+__device__ __forceinline__ void Acc<DT>::float_part(float& hi, float& lo) const {
+    hi = f2_lane0(fs);
+    lo = f2_lane0(fe);
+    df_add(hi, lo, f2_lane1(fs), f2_lane1(fe));
 }
 
 // Shuffle-butterfly reduction of one partial per lane: every lane ends with
@@ -297,7 +308,8 @@ __device__ __forceinline__ void cta_finish(const Acc<DT>& acc, bool folds, uint3
     if (folds) {
         uint32_t s = acc.s;
         uint64_t x = (static_cast<uint64_t>(acc.xh) << 32) | acc.xl, n = acc.n;
-        float hi = acc.fs, lo = acc.fe;
+        float hi = 0.0f, lo = 0.0f;
+        if constexpr (DT != SL_U32) acc.float_part(hi, lo);
         warp_merge<DT>(s, x, n, hi, lo);
         if (lane == 0) {
             WarpPartial p;

@@ -30,7 +30,7 @@ struct KArgs {
     uint32_t tile_vec;      // 16-byte vectors per tile (LDG: cta*K, CPASYNC: cta*D,
                             // TMA: stage_bytes/16)
     int32_t desc;           // 1: walk tiles from the last one downward
-    int32_t nst;            // TMA: ring stages
+    int32_t nst;            // TMA: ring stages (per CTA or per warp)
     int32_t debug;          // SL_DEBUG_* flags
     WarpPartial* parts;     // [grid]: one partial per CTA
     uint64_t* window;       // [2]: earliest CTA start, latest CTA end
@@ -58,6 +58,7 @@ const void* ldg_dyn_kernel(int dtype, int k, int cta);
 const void* cpasync_kernel(int dtype, int d);
 const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
+const void* tma_warp_kernel(int dtype);
 const void* ldg4_kernel(int dtype, int k, int cta);
 const void* ldg32_kernel(int dtype, int k, int cta, bool dyn);
 const void* ldg_fixed_kernel(int dtype, int k, int cta);
@@ -71,6 +72,7 @@ const void* ldg_fixed_cov_kernel(int k, int cta);
 const void* cpasync_cov_kernel(int d);
 const void* ldsts_cov_kernel(int g);
 const void* tma_cov_kernel();
+const void* tma_warp_cov_kernel();
 
 // Two co-resident streams in one CTA (k_two.cu).  Stream A = warps
 // [0, warps_a), stream B = the warps_b warps after them; one CTA per SM.

@@ -14,7 +14,8 @@ from __future__ import annotations
 import statistics
 from dataclasses import dataclass, field
 
-from . import (SL_ASC, SL_CPASYNC, SL_LDG, SL_LDG32, SL_OK, SL_TMA, SL_U32, SLError, config, sl_plan, sl_sweep)
+from . import (SL_ASC, SL_CPASYNC, SL_LDG, SL_LDG32, SL_OK, SL_RING_CTA, SL_RING_WARP, SL_TMA, SL_U32, SLError,
+               config, sl_plan, sl_sweep)
 
 MECH_NAMES = {SL_LDG: "ldg", SL_CPASYNC: "cpasync", SL_TMA: "tma", SL_LDG32: "ldg32"}
 
@@ -27,6 +28,7 @@ class Point:
     grid: int = 0
     stage_bytes: int = 0  # TMA
     stages: int = 0       # TMA
+    ring: int = SL_RING_CTA  # TMA: one ring per CTA or per warp
     cop: int = 0
     order: int = 0        # SL_ASC, or SL_DYN (dynamic contiguous chunks, LDG)
     gbs: list = field(default_factory=list)  # per repeat
@@ -39,7 +41,8 @@ class Point:
     def cfg(self, **kw):
         """The point's sl_config; keyword arguments override its fields."""
         if self.mech == SL_TMA:
-            base = dict(cta=self.cta, grid=self.grid, stage_bytes=self.stage_bytes, stages=self.stages)
+            base = dict(cta=self.cta, grid=self.grid, stage_bytes=self.stage_bytes, stages=self.stages,
+                        ring=self.ring)
         else:
             base = dict(k=self.k, cta=self.cta, grid=self.grid, cop=self.cop)
             if self.order:
@@ -70,12 +73,13 @@ class Point:
     def offered(self) -> int:
         """Offered in-flight bytes per CTA (for tie-breaking)."""
         if self.mech == SL_TMA:
-            return self.stage_bytes * self.stages
+            return self.stage_bytes * self.stages * (self.cta // 32 if self.ring == SL_RING_WARP else 1)
         return self.k * self.cta * (32 if self.mech == SL_LDG32 else 16)
 
     def label(self) -> str:
         if self.mech == SL_TMA:
-            return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}"
+            ring = " warp-rings" if self.ring == SL_RING_WARP else ""
+            return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}{ring}"
         dyn = " dyn" if self.order == 2 else ""
         kd = "D" if self.mech == SL_CPASYNC else "K"
         return f"{MECH_NAMES[self.mech]} {kd}={self.k} cta={self.cta} cop={self.cop}{dyn}"
@@ -83,7 +87,7 @@ class Point:
     def spec(self) -> str:
         """The point in parse_point's notation."""
         if self.mech == SL_TMA:
-            return f"tma:{self.stage_bytes}:{self.stages}:{self.cta}"
+            return f"{'tmaw' if self.ring == SL_RING_WARP else 'tma'}:{self.stage_bytes}:{self.stages}:{self.cta}"
         name = MECH_NAMES[self.mech] + ("dyn" if self.order == 2 else "")
         if self.mech == SL_LDG and self.order != 2:
             return f"ldg:{self.k}:{self.cta}:{self.cop}"
@@ -96,16 +100,22 @@ class Point:
         if self.step_gbs:
             d.update(steps_gbs_median=round(self.step_median, 1), steps_overlapped=self.overlapped)
         if self.mech == SL_TMA:
-            d.update(stage_bytes=self.stage_bytes, stages=self.stages)
+            d.update(stage_bytes=self.stage_bytes, stages=self.stages,
+                     ring="warp" if self.ring == SL_RING_WARP else "cta")
         else:
             d.update(k=self.k, cop=self.cop, order=self.order)
         return d
 
 
 def parse_point(text: str) -> Point:
-    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta' or
-    'tma:stage_bytes:stages:cta'."""
+    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta',
+    'tma:stage_bytes:stages:cta' (one ring per CTA) or 'tmaw:stage_bytes:stages[:cta]' (one ring per
+    warp; cta defaults to warp_ring_cta)."""
     f = text.split(":")
+    if f[0] == "tmaw":
+        sb, n = int(f[1]), int(f[2])
+        return Point(SL_TMA, stage_bytes=sb, stages=n, ring=SL_RING_WARP,
+                     cta=int(f[3]) if len(f) > 3 else warp_ring_cta(sb, n))
     if f[0] in ("ldgdyn", "ldg32dyn", "ldg32"):
         return Point(SL_LDG32 if f[0].startswith("ldg32") else SL_LDG, k=int(f[1]),
                      cta=int(f[2]) if len(f) > 2 else 256, order=2 if f[0].endswith("dyn") else 0)
@@ -118,16 +128,40 @@ def parse_point(text: str) -> Point:
     raise ValueError(f"bad point {text!r}")
 
 
+# shared memory a CTA may use (the GB300 opt-in limit is 227 KiB), less room
+# for the kernels' static shared memory
+SMEM_BUDGET = 227 * 1024 - 4096
+
+
+def warp_ring_cta(stage_bytes: int, stages: int, max_warps: int = 32) -> int:
+    """CTA size of a one-ring-per-warp TMA point: as many warps as fit one
+    CTA's shared memory (each warp holds stages x (stage_bytes + 8) bytes),
+    at least one warp."""
+    per_warp = stages * (stage_bytes + 8)
+    return 32 * max(1, min(max_warps, SMEM_BUDGET // per_warp))
+
+
+TMA_STAGE_BYTES = (4096, 16384, 65536)
+TMA_STAGES = tuple(range(2, 9))
+
+
 def default_points(cta: int = 256) -> list[Point]:
-    pts = [Point(SL_LDG, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8, 12, 16)]
+    """The K-response catalogue: LDG K 1-16 (16 bytes, .cg), four .L2::256B
+    points, the dynamic-chunk traversal, 32-byte loads, cp.async D 1-8, and
+    TMA stage sizes 4/16/64 KiB x 2-8 stages in both ring layouts (one ring
+    per CTA at `cta` consumer threads; one ring per warp at warp_ring_cta).
+    Points whose shared memory does not fit are kept and recorded as
+    infeasible by measure()."""
+    pts = [Point(SL_LDG, k=k, cta=cta) for k in range(1, 17)]
     pts += [Point(SL_LDG, k=k, cta=cta, cop=1) for k in (1, 2, 4, 8)]
-    pts += [Point(SL_LDG, k=k, cta=cta, order=2) for k in (2, 3, 4, 6, 8, 12, 16)]
+    pts += [Point(SL_LDG, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8, 12, 16)]
     pts += [Point(SL_LDG, k=k, cta=512, order=2) for k in (2, 4)]
-    pts += [Point(SL_LDG32, k=k, cta=cta) for k in (1, 2, 4)]
+    pts += [Point(SL_LDG32, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_LDG32, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8)]
-    pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in (1, 2, 4, 8)]
-    pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n)
-            for s in (4096, 16384, 65536) for n in (2, 4, 8) if s * n <= 227 * 1024]
+    pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in range(1, 9)]
+    pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n) for s in TMA_STAGE_BYTES for n in TMA_STAGES]
+    pts += [Point(SL_TMA, cta=warp_ring_cta(s, n), stage_bytes=s, stages=n, ring=SL_RING_WARP)
+            for s in TMA_STAGE_BYTES for n in TMA_STAGES]
     return pts
 
 

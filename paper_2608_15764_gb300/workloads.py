@@ -12,6 +12,11 @@ both the CUDA path and the CPU oracle can be fed the same bytes from it.
   saturating, of 8 x the float32 (seed 4).
 * ``batch_sizes(...)`` -- the 1,024 log-uniform buffer sizes (seed 5) scaled so
   they add up to a fixed total.
+* Adversarial float payloads, built from bit patterns: ``bf16_cancel`` (large
+  values that cancel inside each vector next to small ones),
+  ``bf16_wide`` (magnitudes spread over ~36 binades with cancelling pairs),
+  ``bf16_code_groups`` (every finite bfloat16 code, grouped so that no sum
+  can overflow FP32) and ``fp8_finite_codes`` (every finite E4M3 code).
 
 The heavy lifting is in ``csrc/workloads.c``; large requests are split into
 chunks generated on host threads (the generator is counter-based, so a chunk
@@ -219,3 +224,89 @@ def chase_chain(n: int, stride_bytes: int = 64, seed: int = 6) -> np.ndarray:
     if _load().wl_chase_chain(seed, n, sw, out.ctypes.data, perm.ctypes.data) != 0:
         raise ValueError("chain too large for 32-bit word indices")
     return out
+
+
+# ---- adversarial float payloads (bit patterns only) -------------------------------
+
+def bf16_code(e: int, m: int = 0, neg: bool = False) -> int:
+    """bfloat16 code of (-1)^neg * (1 + m/128) * 2^e, for a normal exponent e
+    (-126..127) and mantissa m (0..127)."""
+    assert -126 <= e <= 127 and 0 <= m < 128
+    return (0x8000 if neg else 0) | ((e + 127) << 7) | m
+
+
+# Eight bfloat16 values whose plain left-to-right FP32 sum loses the small
+# one: 2^20 + 2^-5 rounds to 2^20 in FP32, so 2^-5 disappears in some orders.
+CANCEL_CODES = (bf16_code(-5), bf16_code(20, neg=True), bf16_code(0), bf16_code(20), 0, 0, 0, 0)
+
+
+def bf16_cancel(nvec: int, seed: int = 7, nperm: int = 64) -> np.ndarray:
+    """nvec 16-byte vectors of bfloat16 (8 codes each): vector i holds the
+    codes of CANCEL_CODES in permutation i mod nperm (seeded), so the large
+    pair, the small value and the zeros occupy every position.  Exact sum:
+    nvec * (1 + 2^-5)."""
+    rng = np.random.default_rng(seed)
+    base = np.array(CANCEL_CODES, dtype=np.uint16)
+    perms = np.stack([base[rng.permutation(8)] for _ in range(nperm)])
+    reps = -(-nvec // nperm)
+    return np.ascontiguousarray(np.tile(perms, (reps, 1))[:nvec].reshape(-1))
+
+
+def bf16_wide(nvec: int, seed: int = 8) -> np.ndarray:
+    """nvec 16-byte vectors of bfloat16 spanning ~36 binades: in every vector
+    two random positions hold +L and -L (L = (1 + m/128) 2^e, e in 8..24) and
+    the six others small positive values (e in -12..4), so the exact sum is
+    the sum of the small values while every running FP32 sum is dominated by
+    the large ones."""
+    rng = np.random.default_rng(seed)
+    e = rng.integers(-12, 5, size=(nvec, 8))
+    m = rng.integers(0, 128, size=(nvec, 8))
+    codes = ((e + 127) << 7) | m
+    order = np.argsort(rng.random((nvec, 8)), axis=1)
+    el = rng.integers(8, 25, size=nvec)
+    ml = rng.integers(0, 128, size=nvec)
+    big = ((el + 127) << 7) | ml
+    rows = np.arange(nvec)
+    codes[rows, order[:, 0]] = big
+    codes[rows, order[:, 1]] = big | 0x8000
+    return np.ascontiguousarray(codes.astype(np.uint16).reshape(-1))
+
+
+def bf16_as_f32_bits(codes: np.ndarray) -> np.ndarray:
+    """The float32 payload holding exactly the values of the given bfloat16
+    codes (a bfloat16 is the top half of the float32 with its value)."""
+    return (np.asarray(codes, dtype=np.uint32) << 16).view(np.float32)
+
+
+def bf16_code_groups(limit_log2: int = 127) -> list[np.ndarray]:
+    """Every finite bfloat16 code (both zeros, subnormals and all normal
+    binades, both signs) exactly once, split into groups of one sign and one
+    binade; a binade is split further, in mantissa order, where its values
+    would add up to more than 2^limit_log2.  Within a group every value is an
+    integer multiple of the binade's unit 2^(E-134) (2^-133 for subnormals)
+    and the multiples add up to less than 2^15, so every partial sum of a
+    group, in any order, is exactly representable in FP32 and below the
+    FP32 maximum.  Grouping uses integer arithmetic on the code fields only.
+    The two zeros join the subnormal groups."""
+    groups = []
+    for neg in (0, 1):
+        sign = 0x8000 if neg else 0
+        groups.append(np.array([sign | m for m in range(0, 128)], dtype=np.uint16))  # zero + subnormals
+        for big_e in range(1, 255):
+            # value of mantissa m: (128 + m) * 2^(big_e - 134)
+            cur, acc = [], 0
+            for m in range(128):
+                mult = 128 + m
+                if cur and big_e - 134 + math.log2(acc + mult) > limit_log2:
+                    groups.append(np.array(cur, dtype=np.uint16))
+                    cur, acc = [], 0
+                cur.append(sign | (big_e << 7) | m)
+                acc += mult
+            groups.append(np.array(cur, dtype=np.uint16))
+    return groups
+
+
+def fp8_finite_codes() -> np.ndarray:
+    """Every finite FP8 E4M3 code (all 256 but the two NaNs 0x7F and 0xFF):
+    both zeros, the subnormals and +-448."""
+    return np.array([c for c in range(256) if (c & 0x7F) != 0x7F], dtype=np.uint8)

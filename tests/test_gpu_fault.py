@@ -26,11 +26,12 @@ def sl():
     return sl
 
 
-def test_tma_unarmed_stage_times_out_and_context_survives(sl):
+@pytest.mark.parametrize("ring,stage", [("cta", 16384), ("warp", 4096)])
+def test_tma_unarmed_stage_times_out_and_context_survives(sl, ring, stage):
     nbytes = 1 << 20
     host = workloads.splitmix_u32(9, nbytes // 4)
     dev = torch.from_numpy(host.view(np.uint8)).cuda()
-    bad = sl.config("tma", cta=128, grid=4, stage_bytes=16384, stages=4,
+    bad = sl.config("tma", cta=128, grid=4, stage_bytes=stage, stages=4, ring=ring,
                     debug_flags=sl.SL_DEBUG_TMA_SKIP_STAGE)
     for _ in range(2):
         with pytest.raises(sl.SLError) as e:
@@ -39,6 +40,7 @@ def test_tma_unarmed_stage_times_out_and_context_survives(sl):
         assert "timed out" in sl.sl_last_error()
         # the same context still computes correct results, and the error
         # word was cleared for the next launch
-        r = sl.sl_run(dev, dtype=sl.SL_U32, cfg=sl.config("tma", cta=128, grid=4, stage_bytes=16384, stages=4))
+        r = sl.sl_run(dev, dtype=sl.SL_U32, cfg=sl.config("tma", cta=128, grid=4, stage_bytes=stage, stages=4,
+                                                          ring=ring))
         assert r.status == 0 and (r.sum_u32, r.xor_u64) == oracle.checksum(host)
     torch.cuda.synchronize()

@@ -107,6 +107,12 @@ def test_tma_float(sl, payloads, dt, stage, stages):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("stage,stages,cta", [(4096, 8, 224), (4096, 2, 864), (16384, 3, 128), (65536, 2, 32)])
+def test_tma_warp_rings_float(sl, payloads, dt, stage, stages, cta):
+    _check(sl, payloads[dt], dt, sl.config("tma", cta=cta, stage_bytes=stage, stages=stages, ring="warp"))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 def test_float_closed_forms(sl, dt):
     """Payloads whose exact sum is known: +v/-v pairs sum to zero; a constant
     payload sums to n*c."""

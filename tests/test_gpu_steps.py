@@ -48,6 +48,8 @@ def _results(sl, out, n):
     ("ldg32", dict(k=6, cta=256, order="dyn"), 32),
     ("tma", dict(cta=256, stage_bytes=16384, stages=4), 16), ("tma", dict(cta=512, stage_bytes=65536, stages=2,
                                                                          order="desc"), 16),
+    ("tma", dict(cta=224, stage_bytes=4096, stages=8, ring="warp"), 16),
+    ("tma", dict(cta=96, stage_bytes=16384, stages=4, ring="warp", order="desc"), 16),
 ])
 def test_steps_each_pass_matches_oracle(sl, data, mech, kw, loads):
     dev, _, want = data
@@ -178,13 +180,14 @@ def test_dynamic_steps_float_sums(sl):
         assert abs(r.fsum - ref) <= 2e-6 * abs(ref)
 
 
-def test_tma_steps_report_a_timeout_on_its_own_pass(sl, data):
+@pytest.mark.parametrize("ring,cta,stage", [("cta", 256, 16384), ("warp", 224, 4096)])
+def test_tma_steps_report_a_timeout_on_its_own_pass(sl, data, ring, cta, stage):
     """A TMA pass whose bounded wait gives up (debug flag: one stage never
     armed) reports SL_ERR_TIMEOUT in its own result, and the passes before and
     after it -- overlapped with it -- are unaffected."""
     dev, _, want = data
-    ok = sl.config("tma", cta=256, stage_bytes=16384, stages=4)
-    bad = sl.config("tma", cta=256, stage_bytes=16384, stages=4, debug_flags=sl.SL_DEBUG_TMA_SKIP_STAGE)
+    ok = sl.config("tma", cta=cta, stage_bytes=stage, stages=4, ring=ring)
+    bad = sl.config("tma", cta=cta, stage_bytes=stage, stages=4, ring=ring, debug_flags=sl.SL_DEBUG_TMA_SKIP_STAGE)
     out = torch.zeros(7 * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     rb = sl.RESULT_BYTES
     sl.sl_enqueue_steps(dev, out[: 3 * rb], 3, dtype=sl.SL_U32, cfg=ok)

@@ -113,3 +113,70 @@ def test_chase_chain_is_one_cycle(n, stride):
         idx = int(c[idx])
     assert idx == 0 and len(seen) == n           # a single cycle through every element
     assert np.array_equal(c, wl.chase_chain(n, stride))
+
+
+# ---- adversarial float payloads ----------------------------------------------------
+
+def _bf16_values(codes):
+    """bfloat16 codes -> float64 values through torch's own bfloat16 type."""
+    t = torch.from_numpy(np.ascontiguousarray(codes, dtype=np.uint16).view(np.int16)).view(torch.bfloat16)
+    return t.to(torch.float64).numpy()
+
+
+def test_bf16_code_helper_matches_torch():
+    for e, m, neg in [(0, 0, False), (-5, 0, False), (20, 0, True), (127, 127, False), (-126, 1, True)]:
+        v = _bf16_values([wl.bf16_code(e, m, neg)])[0]
+        assert v == (-1) ** neg * (1 + m / 128) * 2.0 ** e
+
+
+def test_bf16_cancel_pattern():
+    n = 1000
+    c = wl.bf16_cancel(n)
+    v = _bf16_values(c).reshape(n, 8)
+    # every vector holds the same multiset, in many different orders
+    assert all(sorted(r) == sorted([2.0 ** -5, -2.0 ** 20, 1.0, 2.0 ** 20, 0, 0, 0, 0]) for r in v)
+    # each of the four non-zero values appears in every one of the 8 positions
+    for x in (2.0 ** -5, -2.0 ** 20, 1.0, 2.0 ** 20):
+        assert set(np.nonzero(v == x)[1].tolist()) == set(range(8))
+    assert math.fsum(v.reshape(-1)) == n * (1 + 2.0 ** -5)
+    # a plain left-to-right FP32 sum of some vectors loses the 2^-5
+    lossy = [r for r in v.astype(np.float32) if np.float32(np.cumsum(r, dtype=np.float32)[-1]) != np.float32(1 + 2.0 ** -5)]
+    assert lossy
+
+
+def test_bf16_wide_structure():
+    n = 4096
+    v = _bf16_values(wl.bf16_wide(n)).reshape(n, 8)
+    big = np.abs(v) >= 2.0 ** 8
+    assert (big.sum(axis=1) == 2).all()
+    assert np.all(v[big].reshape(n, 2).sum(axis=1) == 0)  # +L and -L in every vector
+    small = v[~big]
+    assert small.min() >= 2.0 ** -12 and small.max() < 2.0 ** 5
+    f32 = wl.bf16_as_f32_bits(wl.bf16_wide(n)).astype(np.float64)
+    assert np.array_equal(f32, v.reshape(-1))
+
+
+def test_bf16_code_groups_cover_every_finite_code_once():
+    groups = wl.bf16_code_groups()
+    allc = np.concatenate(groups)
+    finite = [c for c in range(1 << 16) if (c >> 7) & 0xFF != 0xFF]
+    assert sorted(allc.tolist()) == finite
+    fmax = float(torch.finfo(torch.float32).max)
+    for g in groups:
+        v = _bf16_values(g)
+        assert len(set(np.sign(v[v != 0]))) <= 1  # one sign per group
+        # every value a multiple of one power-of-two unit, multiples adding up
+        # to < 2^15: every partial sum in any order is exact in FP32
+        e = (int(g[-1]) >> 7) & 0xFF
+        unit = 2.0 ** (e - 134) if e else 2.0 ** -133
+        mult = np.abs(v) / unit
+        assert np.all(mult == np.round(mult)) and mult.sum() < 2 ** 15
+        assert math.fsum(np.abs(v)) <= fmax
+
+
+def test_fp8_finite_codes():
+    c = wl.fp8_finite_codes()
+    assert c.size == 254 and 0x7F not in c and 0xFF not in c
+    v = torch.from_numpy(c).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.isfinite(v).all() and v.max() == 448 and v.min() == -448
+    assert (v == 0).sum() == 2 and np.abs(v[v != 0]).min() == 2.0 ** -9
