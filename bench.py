@@ -1,24 +1,42 @@
 #!/usr/bin/env python3
 """Benchmark of the streaming global-load path on GB300.
 
-Workload: a 4 GiB buffer of uint32 words from splitmix64(seed=1) (larger than
-the 129 MB L2, so no flush is needed between steps).  Before timing, the
-K-response curves of the mechanisms (LDG K at 16 and 32 bytes, grid-stride and
-dynamic chunks; cp.async D; TMA stage x stages) are measured on the same
-buffer as single launches, then every point's throughput over 16 back-to-back
-passes, and the fastest point for back-to-back passes is chosen
-(tune.choose(steps=True)).  One step = one checksum pass over the whole
-buffer with that point: one load kernel, whose last CTA to finish combines
-the per-CTA partials into the result.  Passes of grid-stride points run as
-programmatic dependent launches (``sl_enqueue_steps``: a pass starts loading
-while the previous pass's tail runs); other points use one ``sl_enqueue`` per
-pass.
+Headline workload: a 4 GiB buffer of uint32 words from splitmix64(seed=1)
+(larger than the 129 MB L2, so no flush is needed between steps).  Before
+timing, the K-response curves of the mechanisms (LDG K 1-16 at 16 and 32
+bytes, grid-stride and dynamic chunks; cp.async D 1-8; TMA 4/16/64 KiB x 2-8
+stages in both ring layouts) are measured on the same buffer as single
+launches, then every point's throughput over 16 back-to-back passes, and the
+fastest point for back-to-back passes is chosen (tune.choose(steps=True)).
+One step = one checksum pass over the whole buffer with that point: one load
+kernel, whose last CTA to finish combines the per-CTA partials into the
+result.  Passes run as programmatic dependent launches
+(``sl_enqueue_steps``: a pass starts loading while the previous pass's tail
+runs).  After the K timed steps, blocks of K steps are timed for about two
+more seconds with the clocks sampled throughout (the within-run spread).
+
+On one GPU the same JSON line also carries, measured in the same run:
+
+* ``allocation_sweep`` -- LDG K 1/2/4/8/16 over 512 MiB ... 20 GiB buffers in
+  both sweep orders, the K=2->8 change per size, every cell checked against
+  the oracle, whose host-core time is reported beside it;
+* ``precision`` -- the precision form: 4 GiB float payloads (FP32, BF16,
+  FP8-E4M3 x8, and an adversarial BF16 payload whose large values cancel
+  inside every vector) through LDG, cp.async and TMA points, each sum's error
+  against the FP64 oracle;
+* ``batched`` -- the batched form: 1,024 buffers, 16 GiB per dtype, in one
+  autotuned CUDA-graph launch, against 1,024 per-buffer launches in two
+  forms (LDG K=2 at 4 x SMs CTAs on one stream; and each buffer's tuned class
+  configuration with grid = min(resident CTAs x SMs, tiles), captured as one
+  CUDA graph of 1,024 launches).
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+                    [--skip-extras] [--workload stream|batch|prec]
 
 Prints one JSON line (rank 0).  N > 1 (torchrun): every rank streams its own
 4 GiB buffer on its own GPU (weak scaling, no data-path collective); the
-barrier and the max over ranks of the timed interval use torch.distributed.
+barrier and the max over ranks of the timed interval use torch.distributed;
+the single-GPU extras are not run.
 
 ``--impl reference`` times the CPU oracle (``oracle/``) on the host cores over
 the same workload instead; it is the deliberately slow baseline arm.
@@ -59,7 +77,12 @@ def _args(argv=None):
     ap.add_argument("--workload", choices=["stream", "batch", "prec"], default="stream",
                     help="stream: the 4 GiB K-response workload (default); batch: the 1,024-buffer batched form; "
                          "prec: the precision form (float payloads through every mechanism)")
-    ap.add_argument("--prec-gib", type=float, default=1.0, help="prec workload payload size per dtype")
+    ap.add_argument("--prec-gib", type=float, default=4.0, help="precision form: payload size per dtype")
+    ap.add_argument("--alloc-gib", default="0.5,1,2,4,8,16,20", help="allocation sweep sizes in GiB")
+    ap.add_argument("--spread-seconds", type=float, default=2.0,
+                    help="seconds of extra K-step blocks timed after the headline steps")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="headline only (no allocation sweep, precision or batched form)")
     ap.add_argument("--dtypes", default="f32,bf16,fp8", help="batch workload payload dtypes")
     ap.add_argument("--batch-gib", type=float, default=16.0, help="batch workload total per dtype")
     ap.add_argument("--choice", default=None,
@@ -294,21 +317,15 @@ def run_ours(a):
     else:
         choice = [0]
     best = points[replicas.broadcast_choice(choice[0], dist)]
-    cfg = best.cfg()
+    cfg = best.cfg(grid=0)  # one full wave of CTAs per pass
 
-    # ---- timed steps: one pass per step.  Where the point allows it the
-    # passes are programmatic dependent launches (sl_enqueue_steps: a pass
-    # starts loading while the previous pass's tail runs), else one
-    # sl_enqueue per pass.
+    # ---- timed steps: one pass per step, as programmatic dependent launches
+    # (sl_enqueue_steps: a pass starts loading while the previous pass's tail
+    # runs)
     dev_out = torch.zeros((a.warmup + a.steps) * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     rb = sl.RESULT_BYTES
-    if best.overlapped:
-        cfg = best.cfg(grid=0)  # one full wave of CTAs per pass
-        sl.sl_enqueue_steps(bufs, dev_out, a.warmup, dtype=sl.SL_U32, cfg=cfg)
-    else:
-        for i in range(a.warmup):
-            sl.sl_enqueue(bufs[i % 2], dev_out[rb * i:], dtype=sl.SL_U32, cfg=cfg)
+    sl.sl_enqueue_steps(bufs, dev_out, a.warmup, dtype=sl.SL_U32, cfg=cfg)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -316,30 +333,34 @@ def run_ours(a):
     clocks = ClockSampler(info["device"])
     if rank == 0:
         clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
-    if best.overlapped:
-        sl.sl_enqueue_steps(bufs, dev_out[rb * a.warmup:], a.steps, dtype=sl.SL_U32, cfg=cfg)
-        ev[a.steps].record(stream)
-    else:
-        for i in range(a.steps):
-            sl.sl_enqueue(bufs[i % 2], dev_out[rb * (a.warmup + i):], dtype=sl.SL_U32, cfg=cfg)
-            ev[i + 1].record(stream)
+    sl.sl_enqueue_steps(bufs, dev_out[rb * a.warmup:], a.steps, dtype=sl.SL_U32, cfg=cfg)
+    ev[1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    total_ms = ev[0].elapsed_time(ev[1])
+    # within-run spread: more blocks of `steps` passes, each timed on its own,
+    # for about spread_seconds, with the clock sampler still running
+    spread_out = torch.zeros(a.steps * rb, dtype=torch.uint8, device="cuda")
+    blocks, t_end = [], time.perf_counter() + a.spread_seconds
+    while time.perf_counter() < t_end or len(blocks) < 5:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sl.sl_enqueue_steps(bufs, spread_out, a.steps, dtype=sl.SL_U32, cfg=cfg)
+        e1.record(stream)
+        e1.synchronize()
+        blocks.append(e0.elapsed_time(e1))
     clk = clocks.stop() if rank == 0 else None
-    total_ms = ev[0].elapsed_time(ev[a.steps])
-    step_ms = ([total_ms / a.steps] * a.steps if best.overlapped
-               else [ev[i].elapsed_time(ev[i + 1]) for i in range(a.steps)])
     total_ms = replicas.max_over_ranks(total_ms, dist, device="cuda")
     value = replicas.job_gbs(nbytes, a.steps, world, total_ms)
 
     # results of every timed step must agree, and so must the ranks (each
     # streams an identical buffer)
-    raw = dev_out.cpu().numpy().tobytes()
-    res = [sl.sl_result.from_buffer_copy(raw[rb * i:rb * (i + 1)]) for i in range(a.warmup + a.steps)]
+    raw = dev_out.cpu().numpy().tobytes() + spread_out.cpu().numpy().tobytes()
+    res = [sl.sl_result.from_buffer_copy(raw[rb * i:rb * (i + 1)]) for i in range(a.warmup + 2 * a.steps)]
     ck = {(r.sum_u32, r.xor_u64, r.issued_loads, r.status) for r in res}
     consistent = len(ck) == 1 and res[0].issued_loads == best.loads(nbytes) and res[0].status == 0
     per_rank = replicas.gather_results(res[-1].sum_u32, res[-1].xor_u64, res[-1].issued_loads, dist, device="cuda")
@@ -356,7 +377,7 @@ def run_ours(a):
     # place over the CPU-GPU link (longer latency: more bytes in flight).  The
     # faster measured mode is reported.
     host = host_buffer(nbytes, pinned=True)
-    e2e_cands = [("staged", best.label(), cfg)]
+    e2e_cands = [("staged", best.label(), best.cfg())]
     for label, pt in [("direct", "ldgdyn:16:256"), ("direct", "ldgdyn:8:512"), ("direct", "ldgdyn:12:256"),
                       ("direct", "tma:65536:3:256"), ("direct", "tma:16384:8:512")]:
         p = tune.parse_point(pt)
@@ -385,20 +406,28 @@ def run_ours(a):
     words = host.numpy().view("uint32")
     oc, cpu_gbs, threads, passes, el = cpu_oracle(words, a.cpu_seconds)
     parity = (res[0].sum_u32, res[0].xor_u64) == oc and (rh.sum_u32, rh.xor_u64) == oc and e2e_host_ok
+    del host
 
     peak, peak_kind = _peaks()
-    kern_ms = statistics.mean(step_ms)
-    achieved = nbytes / (kern_ms * 1e6)
+    achieved = nbytes * a.steps / (total_ms * 1e6)
     traffic, traffic_note = _traffic(best.label(), nbytes)
+    bgbs = sorted(nbytes * a.steps / (ms * 1e6) for ms in blocks)
+    spread = {"blocks": len(blocks), "steps_per_block": a.steps, "seconds": round(sum(blocks) / 1e3, 2),
+              "gbs_median": round(statistics.median(bgbs), 1), "gbs_min": round(bgbs[0], 1),
+              "gbs_max": round(bgbs[-1], 1), "gbs_p10": round(bgbs[len(bgbs) // 10], 1),
+              "gbs_p90": round(bgbs[(9 * len(bgbs)) // 10], 1),
+              "all_results_match": bool(consistent)}
+    if clk:
+        ms_step = statistics.median(blocks) / a.steps
+        spread.update(sm_mhz_median=clk["sm_mhz"], clock_samples=clk["samples"],
+                      ms_per_step_x_mhz=round(ms_step * clk["sm_mhz"], 1))
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "bytes": nbytes, "choice": best.label(), "choice_spec": best.spec(),
-                   "launch": "programmatic dependent launches (sl_enqueue_steps)" if best.overlapped
-                   else "one sl_enqueue per step",
-                   "grid": best.resident * info["sm_count"] if best.overlapped else best.grid_used,
-                   "resident_per_sm": best.resident,
+                   "launch": "programmatic dependent launches (sl_enqueue_steps)",
+                   "grid": best.resident * info["sm_count"], "resident_per_sm": best.resident,
                    "l2": "inputs larger than L2 (4 GiB vs 129 MB), two resident copies read alternately by "
                          "consecutive steps: no flush between steps",
                    "parallelism": f"replicas x{world} (one buffer per GPU)"},
@@ -407,10 +436,9 @@ def run_ours(a):
                      "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} copy (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_kind == "measured" else "fallback", "traffic": traffic,
                      "traffic_note": traffic_note,
-                     "note": ("mean interval per pass of the overlapped launches (programmatic dependent "
-                              "launches, one kernel per pass, CUDA events around the timed passes)"
-                              if best.overlapped else
-                              "per-step CUDA-event time of the load kernel, including its last-CTA combine")},
+                     "note": "mean interval per pass of the overlapped launches (programmatic dependent "
+                             "launches, one kernel per pass, CUDA events on the launching stream around the "
+                             "timed passes)"},
         "cpu_baseline": {"value": round(cpu_gbs, 2), "unit": "GB/s", "cores": threads, "kind": "oracle",
                          "sample": f"{passes} full passes over the {nbytes >> 20} MiB host buffer "
                                    f"({el:.1f} s wall, {threads} threads)"},
@@ -420,32 +448,234 @@ def run_ours(a):
                 "modes": [{k: v for k, v in e.items() if k != "result"} for e in e2e_all]},
         "gpu_launches": a.steps,
         "clocks": clk,
+        "spread": spread,
         "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent),
                    "ranks_agree": bool(ranks_agree)},
         "curves": [p.as_dict() for p in points],
         "device": {k: info[k] for k in ("name", "sm_count", "l2_bytes", "cc_major", "cc_minor")},
     }
+    del buf, buf2, bufs, dev_out, spread_out
+    torch.cuda.empty_cache()
+    extras_ok = True
+    if world == 1 and not a.skip_extras and not a.choice:
+        line["allocation_sweep"] = alloc_section(a, info)
+        line["precision"] = prec_section(a)
+        line["batched"] = batch_section(a, info)
+        extras_ok = all(line[k]["parity"] for k in ("allocation_sweep", "precision", "batched"))
     print(json.dumps(line), flush=True)
     if a.out:
         with open(a.out, "a") as f:
             f.write(json.dumps(line) + "\n")
     if dist:
         dist.destroy_process_group()
-    return 0 if parity and consistent else 3
+    return 0 if parity and consistent and extras_ok else 3
 
+
+# ---- allocation-size sweep (config c4) -------------------------------------------
+
+ALLOC_K = (1, 2, 4, 8, 16)
+
+
+def oracle_prefix_checksums(seed: int, sizes: list[int], threads: int):
+    """The oracle's checksum of the first s bytes of the splitmix64(seed)
+    buffer for every s in sizes (multiples of 16 MiB), generating and folding
+    16 MiB pieces on the host threads (the checksum of disjoint pieces
+    combines exactly).  Returns ({size: (sum, xor)}, GB/s, seconds)."""
+    import oracle
+    from paper_2608_15764_gb300 import workloads as wl
+    piece = 16 << 20
+    top = max(sizes)
+    assert all(sz % piece == 0 for sz in sizes)
+
+    def one(st):
+        return oracle.checksum(wl.splitmix_u32(seed, piece // 4, first_word=st // 4))
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(one, range(0, top, piece)))
+    el = time.perf_counter() - t0
+    return {sz: oracle.combine(parts[: sz // piece]) for sz in sizes}, top / el / 1e9, el
+
+
+def alloc_section(a, info) -> dict:
+    """Allocation-size sweep (paper §3 "Allocation-size sweep", §4.2 Table 2):
+    one buffer per size (splitmix64 seed 1, filled on the device), LDG K in
+    ALLOC_K at 256 threads and the default grid, every K sweep run ascending
+    and reversed (1 warm-up + 3 timed launches per cell), every launch checked
+    against the oracle's checksum of the same words, generated and folded on
+    the host cores (timed, reported beside the GPU cells)."""
+    import torch
+    import paper_2608_15764_gb300 as sl
+    threads = os.cpu_count() or 1
+    sizes = [int(float(g) * (1 << 30)) for g in a.alloc_gib.split(",")]
+    cks, ogbs, osec = oracle_prefix_checksums(1, sizes, threads)
+    cells = [sl.config("ldg", k=k, cta=256) for k in ALLOC_K]
+    rows, all_ok = [], True
+    clocks = ClockSampler(info["device"])
+    clocks.start()
+    for nb in sizes:
+        dev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        sl.sl_fill_splitmix64(dev, seed=1)
+        row = {"bytes": nb, "gib": nb / (1 << 30)}
+        for order in ("asc", "desc"):
+            res = sl.sl_sweep(dev, cells, dtype=sl.SL_U32, repeats=3, warmup=1, sweep_order=order)
+            per_k, ok = {}, True
+            for k, rr in zip(ALLOC_K, res):
+                per_k[k] = round(statistics.median(nb / r.device_ns for r in rr), 1)
+                ok = ok and all((r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*cks[nb], nb // 16, 0)
+                                for r in rr)
+            row[order] = {"gbs": per_k, "k2_to_k8": round((per_k[8] - per_k[2]) / per_k[2], 4),
+                          "above_datasheet": any(v > DATASHEET_GBS for v in per_k.values()), "parity": ok}
+            all_ok = all_ok and ok
+        rows.append(row)
+        del dev
+        torch.cuda.empty_cache()
+    return {"config": "LDG K 1/2/4/8/16, 256 threads, grid min(4, resident) x SMs, single pass, "
+                      "ascending and reversed K sweeps, 3 timed launches per cell (median)",
+            "sizes": rows, "parity": all_ok, "clocks": clocks.stop(),
+            "oracle": {"gbs": round(ogbs, 2), "seconds": round(osec, 2), "cores": threads,
+                       "what": f"splitmix64 generation + checksum of the largest buffer ({max(sizes) >> 20} MiB; "
+                               "every size's checksum is a prefix of it) on all host cores"},
+            "l2_hit_rate": "not measured in this run (ncu): see the allocation-sweep counter summary in profiles/"}
+
+
+# ---- precision form (config c5 payloads, single buffers) -----------------------------
+
+PREC_METRIC = "attained GB/s of the compensated FP32 sum (FP64 final combine) per payload dtype and mechanism"
+PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
+              [dict(mech="ldg", k=k, cta=256, order="dyn") for k in (2, 4, 8)] +
+              [dict(mech="ldg32", k=k, cta=256, order="dyn") for k in (2, 6)] +
+              [dict(mech="cpasync", k=d, cta=256) for d in (2, 4, 6)] +
+              [dict(mech="tma", stage_bytes=sb, stages=n, cta=256) for sb, n in ((16384, 2), (16384, 4), (65536, 2))] +
+              [dict(mech="tma", stage_bytes=sb, stages=n, cta=32 * n, ring="warp")
+               for sb, n in ((4096, 6), (4096, 8), (16384, 8))])
+
+
+def _prec_payloads(a):
+    """(name, dtype, host array) of the precision form: N(0,1) payloads per
+    dtype and the adversarial BF16 payload (large values cancelling inside
+    every vector next to small ones)."""
+    from paper_2608_15764_gb300 import workloads as wl
+    nbytes = int(a.prec_gib * (1 << 30)) // 16 * 16
+    for name, dt in (("f32", wl.F32), ("bf16", wl.BF16), ("fp8", wl.FP8_E4M3)):
+        yield name, dt, wl.payload(dt, nbytes // wl.ELEM_BYTES[dt])
+    yield "bf16-cancel", wl.BF16, wl.bf16_cancel(nbytes // 16)
+
+
+def prec_section(a) -> dict:
+    """The precision form at full size: each payload through every point of
+    PREC_CELLS, `steps` timed launches each.  The oracle's FP64 Neumaier sum of
+    the same payload on all host cores (one contiguous range per thread, range
+    sums added with math.fsum) is timed and is the reference for the error of
+    every GPU sum, reported relative to |sum| and normalised by sum|x|; the
+    gate is 2e-6 relative, or 2e-6 sum|x| where |sum| < 1e-3 sum|x| / sqrt(n).
+    The uint32 checksum of the raw words is checked bit-exactly too."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2608_15764_gb300 as sl
+    from paper_2608_15764_gb300 import workloads as wl
+
+    threads = os.cpu_count() or 1
+    per, worst_all, all_ok = [], 0.0, True
+    steps = max(3, min(a.steps, 10))
+    for name, dt, host in _prec_payloads(a):
+        n = host.size
+        hb = host.view(np.uint8)
+        nbytes = hb.size
+        cut = [i * (n // threads) // 16 * 16 for i in range(threads)] + [n]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(lambda i: oracle.fsum(dt, host[cut[i]:cut[i + 1]]), range(threads)))
+        cpu_s = time.perf_counter() - t0
+        ref = math.fsum(p[0] for p in parts)
+        absum = math.fsum(p[1] for p in parts)
+        bcut = [c * wl.ELEM_BYTES[dt] for c in cut]
+        with ThreadPoolExecutor(threads) as ex:
+            ck = oracle.combine(ex.map(lambda i: oracle.checksum(hb[bcut[i]:bcut[i + 1]]), range(threads)))
+        dev = torch.from_numpy(hb).cuda()
+        cfgs = [sl.config(c["mech"], **{k: v for k, v in c.items() if k != "mech"}) for c in PREC_CELLS]
+        res = sl.sl_sweep(dev, cfgs, dtype=dt, repeats=steps, warmup=1)
+        points = []
+        small = abs(ref) < 1e-3 * absum / max(n, 1) ** 0.5
+        for c, rr in zip(PREC_CELLS, res):
+            gbs = [nbytes / r.device_ns for r in rr if r.status == 0 and r.device_ns]
+            fs = [r.fsum for r in rr]
+            err = max(abs(f - ref) for f in fs)
+            gated = err / (absum if small else abs(ref))
+            ck_ok = all((r.sum_u32, r.xor_u64, r.status) == (*ck, 0) for r in rr)
+            worst_all = max(worst_all, gated)
+            all_ok = all_ok and ck_ok and gated <= 2e-6
+            points.append({**c, "gbs_median": round(statistics.median(gbs), 1) if gbs else None,
+                           "rel_err": err / abs(ref) if ref else None, "err_over_abs_sum": err / absum,
+                           "gated_err": gated, "checksum_ok": ck_ok, "deterministic": len(set(fs)) == 1})
+        best = max(points, key=lambda p: p["gbs_median"] or 0)
+        per.append({"payload": name, "bytes": nbytes, "ref_fsum": ref, "abs_sum": absum,
+                    "gate": "sum|x|" if small else "|sum|", "best": best, "points": points,
+                    "oracle_gbs": round(nbytes / cpu_s / 1e9, 2)})
+        del dev
+        torch.cuda.empty_cache()
+    value = len(per) / sum(1.0 / p["best"]["gbs_median"] for p in per)
+    cpu = [p["oracle_gbs"] for p in per]
+    return {"metric": PREC_METRIC, "value": round(value, 1), "unit": "GB/s",
+            "config": f"{a.prec_gib:g} GiB payload per dtype (N(0,1), FP8 x8; plus BF16 cancellation), "
+                      f"{steps} timed launches per point",
+            "cpu_baseline": {"value": round(len(cpu) / sum(1.0 / v for v in cpu), 2), "unit": "GB/s",
+                             "cores": threads, "kind": "oracle",
+                             "sample": "one FP64 Neumaier pass over each full payload, split over the host threads"},
+            "roofline": _roofline_simple(value, "harmonic mean over payloads of the fastest point's bytes / "
+                                                "CUDA-event time of one launch"),
+            "per_payload": per, "max_gated_err": worst_all, "parity": bool(all_ok)}
+
+
+def run_prec(a):
+    """--workload prec: the precision form alone, as its own JSON line."""
+    import torch
+    import paper_2608_15764_gb300 as sl
+    rank, _, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    sl.load()
+    sec = prec_section(a)
+    line = {"metric": sec.pop("metric"), "value": sec.pop("value"), "unit": sec.pop("unit"), "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "data": "synthetic",
+            "dtype": "f32,bf16,fp8", **sec}
+    print(json.dumps(line), flush=True)
+    return 0 if line["parity"] else 3
+
+
+# ---- batched form (config c5) ----------------------------------------------------
 
 BATCH_METRIC = "aggregate GB/s, 1,024 uneven buffers in one autotuned CUDA-graph launch vs per-buffer launches"
 
 
-def run_batch(a):
+def _tiles(c, nbytes: int) -> int:
+    """Tiles (work units) of one pass over nbytes at configuration c."""
+    import paper_2608_15764_gb300 as sl
+    if c.mech == sl.SL_TMA:
+        return (nbytes + c.stage_bytes - 1) // c.stage_bytes
+    per = c.cta * c.k
+    return (nbytes // 16 + per - 1) // per
+
+
+def batch_section(a, info) -> dict:
     """Batched precision form: for each payload dtype, 1,024 buffers with
-    log-uniform sizes in 64 KiB - 256 MiB adding up to 16 GiB (N(0,1) payloads,
-    FP8 scaled by 8), placed back to back in one device arena.  The autotuner
-    picks mechanism / K / CTA per size class from measured curves; the batch
-    (one graph launch) is timed against 1,024 per-buffer sl_enqueue launches
-    (LDG K=2, 256 threads, 4 x SMs) queued on one stream with one final sync.
-    Every buffer's uint32 checksum is checked against the oracle, and the
-    float sums of 48 buffers spread over the size range."""
+    log-uniform sizes in 64 KiB - 256 MiB adding up to 16 GiB (N(0,1)
+    payloads, FP8 scaled by 8), back to back in one device arena.  The
+    autotuner picks mechanism / K / CTA per size class from measured curves;
+    the batch (one graph launch) is timed against two per-buffer forms:
+    (a) 1,024 sl_enqueue launches of LDG K=2, 256 threads, 4 x SMs CTAs on one
+    stream with one final sync; (b) each buffer with its class's tuned
+    configuration and grid = min(resident CTAs x SMs, tiles), the 1,024
+    launches captured once as a CUDA graph and replayed.  Every buffer's
+    uint32 checksum (batch and both baselines) is checked against the oracle,
+    whose timed host-core pass over all buffers is the cpu_baseline leg; the
+    float sums of 48 buffers spread over the size range are checked against
+    the oracle's FP64 sums."""
     import numpy as np
     import torch
 
@@ -454,22 +684,37 @@ def run_batch(a):
     from paper_2608_15764_gb300 import autotune
     from paper_2608_15764_gb300 import workloads as wl
 
-    rank, world, local = _dist()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
-    sl.load()
-    info = sl.sl_device_info()
     sizes = wl.batch_sizes(total=int(a.batch_gib * (1 << 30)))
     total = sum(sizes)
-    offs = np.cumsum([0] + sizes[:-1])
+    offs = [int(o) for o in np.cumsum([0] + sizes[:-1])]
     names = {"f32": wl.F32, "bf16": wl.BF16, "fp8": wl.FP8_E4M3, "u32": wl.U32}
-    per, cpu_gbs = [], []
     threads = os.cpu_count() or 1
+    per, cpu_gbs = [], []
     host = torch.empty(total, dtype=torch.uint8, pin_memory=True)
     hv = host.numpy()
     dev = torch.empty(total, dtype=torch.uint8, device="cuda")
     base = dev.data_ptr()
+    rb = sl.RESULT_BYTES
+    sms = info["sm_count"]
+    steps = max(3, min(a.steps, 10))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        out = []
+        for rep in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            if rep:
+                out.append(e0.elapsed_time(e1))
+        return out
+
+    def results(buf_out):
+        raw = buf_out.cpu().numpy().tobytes()
+        return [sl.sl_result.from_buffer_copy(raw[i * rb:(i + 1) * rb]) for i in range(len(sizes))]
+
     for name in a.dtypes.split(","):
         dt = names[name]
         t0 = time.perf_counter()
@@ -480,40 +725,59 @@ def run_batch(a):
         gen_s = time.perf_counter() - t0
         dev.copy_(host)
         torch.cuda.synchronize()
-        bufs = [(base + int(o), nb, dt) for o, nb in zip(offs, sizes)]
+        bufs = [(base + o, nb, dt) for o, nb in zip(offs, sizes)]
         table, report = autotune.tune(bufs, repeats=3)
         b = sl.sl_batch_create(bufs, table)
         for _ in range(a.warmup):
             sl.sl_batch_run(b, results=False)
-        ts = [sl.sl_batch_run(b, results=False)[1] for _ in range(a.steps)]
+        ts = [sl.sl_batch_run(b, results=False)[1] for _ in range(steps)]
         res, _ = sl.sl_batch_run(b)
         batch_gbs = total * len(ts) / sum(ts)
-        # per-buffer launches on one stream, one final sync
-        cfg = sl.config("ldg", k=2, cta=256, grid=4 * info["sm_count"])
-        out = torch.zeros(len(sizes) * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-        stream = torch.cuda.current_stream()
-        plain_ms = []
-        for rep in range(a.warmup + a.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+        # (a) per-buffer launches of one plain configuration, one stream
+        plain_cfg = sl.config("ldg", k=2, cta=256, grid=4 * sms)
+        out_a = torch.zeros(len(sizes) * rb, dtype=torch.uint8, device="cuda")
+
+        def plain():
             for i, (p, nb, _) in enumerate(bufs):
-                sl.sl_enqueue(p, out[i * sl.RESULT_BYTES:], nbytes=nb, dtype=dt, cfg=cfg)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if rep >= a.warmup:
-                plain_ms.append(e0.elapsed_time(e1))
+                sl.sl_enqueue(p, out_a[i * rb:], nbytes=nb, dtype=dt, cfg=plain_cfg)
+        plain_ms = timed(plain, steps)
+        plain_res = results(out_a)
+        # (b) per-buffer launches of each buffer's tuned class configuration,
+        # grid sized to the buffer, captured once as a CUDA graph
+        tuned = []
+        for p, nb, _ in bufs:
+            e = next(e for e in table if e.min_bytes <= nb <= e.max_bytes and e.dtype in (-1, dt))
+            c = e.cfg
+            r = sl.sl_plan(nb, dt, c)
+            grid = max(1, min(r.resident_per_sm * sms, _tiles(c, nb)))
+            kw = dict(cta=c.cta, grid=grid)
+            if c.mech == sl.SL_TMA:
+                kw.update(stage_bytes=c.stage_bytes, stages=c.stages, ring=c.tma_ring)
+            else:
+                kw.update(k=c.k)
+            tuned.append((p, nb, c.mech, kw))
+        out_b = torch.zeros(len(sizes) * rb, dtype=torch.uint8, device="cuda")
+        for p, nb, mech, kw in tuned:  # warm: plans cached, scratch sized, before capture
+            sl.sl_enqueue(p, out_b, nbytes=nb, dtype=dt, cfg=sl.config(mech, **kw))
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for i, (p, nb, mech, kw) in enumerate(tuned):
+                sl.sl_enqueue(p, out_b[i * rb:], nbytes=nb, dtype=dt, cfg=sl.config(mech, **kw))
+        graph_ms = timed(graph.replay, steps)
+        graph_res = results(out_b)
         plain_gbs = total * len(plain_ms) / (sum(plain_ms) * 1e6)
-        raw = out.cpu().numpy().tobytes()
-        plain = [sl.sl_result.from_buffer_copy(raw[i * sl.RESULT_BYTES:(i + 1) * sl.RESULT_BYTES])
-                 for i in range(len(sizes))]
+        graph_gbs = total * len(graph_ms) / (sum(graph_ms) * 1e6)
         # cpu_baseline leg: the oracle's checksum of every buffer on all host
         # cores, timed; its results are also the parity reference
         t0 = time.perf_counter()
         with ThreadPoolExecutor(threads) as ex:
             cks = list(ex.map(lambda i: oracle.checksum(hv[offs[i]:offs[i] + sizes[i]]), range(len(sizes))))
         cpu_gbs.append(total / (time.perf_counter() - t0) / 1e9)
-        ck_ok = all((r.sum_u32, r.xor_u64, r.issued_loads) == (*ck, nb // 16) for r, ck, nb in zip(res, cks, sizes))
-        ck_ok = ck_ok and all((r.sum_u32, r.xor_u64) == ck for r, ck in zip(plain, cks))
+        ck_ok = all((r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*ck, nb // 16, 0)
+                    for r, ck, nb in zip(res, cks, sizes))
+        base_ok = all((r.sum_u32, r.xor_u64, r.status) == (*ck, 0)
+                      for rr in (plain_res, graph_res) for r, ck in zip(rr, cks))
         worst = None
         if dt != wl.U32:
             # gate per buffer: relative to |exact sum|, or to sum|x| when the
@@ -526,23 +790,35 @@ def run_batch(a):
             for i, (ref, absum) in zip(sample, refs):
                 nel = sizes[i] // wl.ELEM_BYTES[dt]
                 small = abs(ref) < 1e-3 * absum / max(nel, 1) ** 0.5
-                errs.append(abs(res[i].fsum - ref) / (absum if small else abs(ref)))
+                for r in (res[i], graph_res[i]):
+                    errs.append(abs(r.fsum - ref) / (absum if small else abs(ref)))
             worst = max(errs)
         sl.sl_batch_destroy(b)
+        del graph
         per.append({"dtype": name, "bytes": total, "batched_gbs": round(batch_gbs, 1),
-                    "batched_ms": round(statistics.median(ts) / 1e6, 4), "per_buffer_gbs": round(plain_gbs, 1),
-                    "per_buffer_ms": round(statistics.median(plain_ms), 4),
-                    "speedup": round(batch_gbs / plain_gbs, 3), "frac_of_datasheet": round(batch_gbs / DATASHEET_GBS, 4),
-                    "checksums_match_oracle": bool(ck_ok), "fsum_max_gated_err_sample48": worst,
-                    "host_generation_s": round(gen_s, 1),
+                    "batched_ms": round(statistics.median(ts) / 1e6, 4),
+                    "per_buffer_gbs": round(plain_gbs, 1), "per_buffer_ms": round(statistics.median(plain_ms), 4),
+                    "per_buffer_tuned_graph_gbs": round(graph_gbs, 1),
+                    "per_buffer_tuned_graph_ms": round(statistics.median(graph_ms), 4),
+                    "speedup": round(batch_gbs / plain_gbs, 3),
+                    "speedup_vs_tuned_graph": round(batch_gbs / graph_gbs, 3),
+                    "frac_of_datasheet": round(batch_gbs / DATASHEET_GBS, 4),
+                    "checksums_match_oracle": bool(ck_ok), "baselines_match_oracle": bool(base_ok),
+                    "fsum_max_gated_err_sample48": worst, "host_generation_s": round(gen_s, 1),
                     "tuning": [{k: r[k] for k in ("class", "buffers", "bytes", "choice", "gbs")} for r in report]})
+    del dev, host
+    torch.cuda.empty_cache()
     all_bytes = sum(p["bytes"] for p in per)
     value = all_bytes / sum(p["bytes"] / p["batched_gbs"] for p in per)
-    line = {"metric": BATCH_METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
-            "warmup": a.warmup, "higher_is_better": True, "data": "synthetic", "dtype": a.dtypes,
+    plain_all = all_bytes / sum(p["bytes"] / p["per_buffer_gbs"] for p in per)
+    graph_all = all_bytes / sum(p["bytes"] / p["per_buffer_tuned_graph_gbs"] for p in per)
+    return {"metric": BATCH_METRIC, "value": round(value, 1), "unit": "GB/s",
+            "per_buffer_gbs": round(plain_all, 1), "per_buffer_tuned_graph_gbs": round(graph_all, 1),
+            "speedup": round(value / plain_all, 3), "speedup_vs_tuned_graph": round(value / graph_all, 3),
             "config": {"workload": f"1,024 buffers, log-uniform 64 KiB-256 MiB, {a.batch_gib:g} GiB per dtype "
                                    "(N(0,1), FP8 x8), one device arena",
-                       "l2": "inputs larger than L2; each buffer read once per launch"},
+                       "l2": "inputs larger than L2; each buffer read once per launch",
+                       "timing": f"{steps} timed graph launches per dtype after {a.warmup} warm-up launches"},
             "cpu_baseline": {"value": round(len(cpu_gbs) / sum(1.0 / v for v in cpu_gbs), 2), "unit": "GB/s",
                              "cores": threads, "kind": "oracle",
                              "sample": "the oracle's uint32 checksum of all 1,024 buffers per dtype, "
@@ -550,99 +826,24 @@ def run_batch(a):
             "roofline": _roofline_simple(value, "aggregate bytes of all buffers / CUDA-event time of the graph "
                                                 "launch (all class kernels and the combine)"),
             "per_dtype": per,
-            "parity": all(p["checksums_match_oracle"] for p in per) and
+            "parity": all(p["checksums_match_oracle"] and p["baselines_match_oracle"] for p in per) and
             all(p["fsum_max_gated_err_sample48"] is None or p["fsum_max_gated_err_sample48"] <= 2e-6 for p in per)}
-    print(json.dumps(line), flush=True)
-    if a.out:
-        with open(a.out, "a") as f:
-            f.write(json.dumps(line) + "\n")
-    return 0 if line["parity"] else 3
 
 
-PREC_METRIC = "attained GB/s of the compensated FP32 sum (FP64 final combine) per payload dtype and mechanism"
-PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
-              [dict(mech="ldg", k=k, cta=256, order="dyn") for k in (2, 4, 8)] +
-              [dict(mech="cpasync", k=d, cta=256) for d in (2, 4, 6)] +
-              [dict(mech="tma", stage_bytes=sb, stages=n, cta=256) for sb, n in ((16384, 2), (16384, 4), (65536, 2))])
-
-
-def run_prec(a):
-    """Precision form: N(0,1) payloads of --prec-gib GiB (float32, bfloat16,
-    FP8-E4M3 x8; inputs larger than L2) through every point of PREC_CELLS,
-    `steps` timed launches each.  cpu_baseline leg: the oracle's FP64
-    Neumaier sum of the same payload on all host cores (one contiguous range
-    per thread, range sums added with math.fsum), timed; it is also the
-    reference for the error of every GPU sum, reported relative to |sum| and
-    normalised by sum|x|.  value = the harmonic mean over dtypes of each
-    dtype's fastest point."""
-    import math
-
-    import numpy as np
+def run_batch(a):
+    """--workload batch: the batched form alone, as its own JSON line."""
     import torch
-
-    import oracle
     import paper_2608_15764_gb300 as sl
-    from paper_2608_15764_gb300 import workloads as wl
-
-    rank, world, local = _dist()
+    rank, _, local = _dist()
     if rank != 0:
         return 0
     torch.cuda.set_device(local)
     sl.load()
-    nbytes = int(a.prec_gib * (1 << 30)) // 16 * 16
-    threads = os.cpu_count() or 1
-    per, cpu = [], []
-    worst_all = 0.0
-    clocks = ClockSampler(local)
-    for dt in (wl.F32, wl.BF16, wl.FP8_E4M3):
-        name = {wl.F32: "f32", wl.BF16: "bf16", wl.FP8_E4M3: "fp8"}[dt]
-        n = nbytes // wl.ELEM_BYTES[dt]
-        host = wl.payload(dt, n)
-        hb = host.view(np.uint8)
-        cut = [i * (n // threads) // 16 * 16 for i in range(threads)] + [n]
-        t0 = time.perf_counter()
-        with ThreadPoolExecutor(threads) as ex:
-            parts = list(ex.map(lambda i: oracle.fsum(dt, host[cut[i]:cut[i + 1]]), range(threads)))
-        cpu_s = time.perf_counter() - t0
-        cpu.append(nbytes / cpu_s / 1e9)
-        ref = math.fsum(p[0] for p in parts)
-        absum = math.fsum(p[1] for p in parts)
-        dev = torch.from_numpy(hb).cuda()
-        cfgs = [sl.config(c["mech"], **{k: v for k, v in c.items() if k != "mech"}) for c in PREC_CELLS]
-        clocks.start()
-        res = sl.sl_sweep(dev, cfgs, dtype=dt, repeats=a.steps, warmup=a.warmup)
-        clk = clocks.stop()
-        points = []
-        for c, rr in zip(PREC_CELLS, res):
-            gbs = [nbytes / r.device_ns for r in rr if r.status == 0 and r.device_ns]
-            fs = [r.fsum for r in rr]
-            err = max(abs(f - ref) for f in fs)
-            small = abs(ref) < 1e-3 * absum / max(n, 1) ** 0.5
-            gated = err / (absum if small else abs(ref))
-            worst_all = max(worst_all, gated)
-            points.append({**c, "gbs_median": round(statistics.median(gbs), 1) if gbs else None,
-                           "rel_err": err / abs(ref), "err_over_abs_sum": err / absum, "gated_err": gated,
-                           "deterministic": len(set(fs)) == 1})
-        best = max(points, key=lambda p: p["gbs_median"] or 0)
-        per.append({"dtype": name, "bytes": nbytes, "ref_fsum": ref, "abs_sum": absum, "best": best,
-                    "points": points, "clocks": clk, "oracle_gbs": round(cpu[-1], 2)})
-        del dev
-        torch.cuda.empty_cache()
-    value = len(per) / sum(1.0 / p["best"]["gbs_median"] for p in per)
-    line = {"metric": PREC_METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": 1, "steps": a.steps,
-            "warmup": a.warmup, "higher_is_better": True, "data": "synthetic", "dtype": "f32,bf16,fp8",
-            "config": {"workload": f"{a.prec_gib:g} GiB N(0,1) payload per dtype (FP8 x8), one launch per step",
-                       "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": round(len(cpu) / sum(1.0 / v for v in cpu), 2), "unit": "GB/s",
-                             "cores": threads, "kind": "oracle",
-                             "sample": "one FP64 Neumaier pass over each full payload, split over the host threads"},
-            "roofline": _roofline_simple(value, "harmonic mean over dtypes of the fastest point's bytes / "
-                                                "CUDA-event time of one launch"),
-            "per_dtype": per, "max_gated_err": worst_all, "parity": worst_all <= 2e-6}
+    sec = batch_section(a, sl.sl_device_info())
+    line = {"metric": sec.pop("metric"), "value": sec.pop("value"), "unit": sec.pop("unit"), "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "higher_is_better": True, "data": "synthetic",
+            "dtype": a.dtypes, **sec}
     print(json.dumps(line), flush=True)
-    if a.out:
-        with open(a.out, "a") as f:
-            f.write(json.dumps(line) + "\n")
     return 0 if line["parity"] else 3
 
 

@@ -110,7 +110,8 @@ typedef struct sl_config {
     int32_t cta;         /* threads per CTA that fold loads, a multiple of 32:
                             32..1024 for LDG/CPASYNC (LDG with K > 8: up to 512);
                             TMA: 32..992 with SL_RING_CTA, which adds one
-                            producer warp; 32..1024 with SL_RING_WARP. */
+                            producer warp; with SL_RING_WARP, cta/32 must
+                            divide `stages`. */
     int32_t grid;        /* CTAs; <= 0 selects min(4, resident CTAs per SM) x SMs */
     int32_t order;       /* sl_order: traversal of the tiles; never changes the
                             integer result */
@@ -149,13 +150,15 @@ typedef struct sl_config {
  *                 stage costs every consumer warp one full-barrier wait and one
  *                 empty-barrier arrive.  Dynamic shared memory stages *
  *                 stage_bytes.
- *   SL_RING_WARP: every warp owns a ring of `stages` stages of stage_bytes,
- *                 filled by its own lane 0 and read by its own 32 lanes only,
- *                 so a stage costs one wait per warp and no cross-warp
- *                 synchronisation (small stages no longer pay a CTA-wide
- *                 protocol per 16 bytes a thread reads).  Chunks are dealt to
- *                 warps grid-wide.  Dynamic shared memory (cta/32) * stages *
- *                 (stage_bytes + 8). */
+ *   SL_RING_WARP: the same CTA ring of `stages` stages, dealt to the CTA's
+ *                 cta/32 warps (no producer warp): each warp owns stages /
+ *                 (cta/32) stages, filled by its own lane 0 and read by its
+ *                 own 32 lanes only, so a stage costs one wait per warp and no
+ *                 cross-warp synchronisation (small stages no longer pay a
+ *                 CTA-wide protocol per 16 bytes a thread reads; a 4 KiB stage
+ *                 gives each lane 8 vectors).  Chunks are dealt to warps
+ *                 grid-wide.  Dynamic shared memory stages * (stage_bytes +
+ *                 8). */
 typedef enum { SL_RING_CTA = 0, SL_RING_WARP = 1 } sl_tma_ring;
 
 #define SL_DEBUG_TMA_SKIP_STAGE 1

@@ -312,11 +312,15 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
         if (cfg->stages < SL_MIN_STAGES || cfg->stages > SL_MAX_STAGES)
             return fail(SL_ERR_ARG, "TMA stages %d not in %d..%d", cfg->stages, SL_MIN_STAGES, SL_MAX_STAGES);
         if (cfg->tma_ring == SL_RING_WARP) {
-            // one ring per warp, filled by the warp's own lane 0; its full
-            // barriers follow the rings in dynamic shared memory
+            // the CTA's stages dealt to its warps, each filled by its warp's
+            // own lane 0; the full barriers follow the stages in dynamic
+            // shared memory
+            if (cfg->stages % (cta / 32) != 0)
+                return fail(SL_ERR_ARG, "SL_RING_WARP deals the %d stages to %d warps: the warp count must divide "
+                            "the stage count", cfg->stages, cta / 32);
             p->fn = sl::tma_warp_kernel(dtype);
             p->block = cta;
-            p->smem = static_cast<size_t>(cta / 32) * cfg->stages * (static_cast<size_t>(cfg->stage_bytes) + 8);
+            p->smem = static_cast<size_t>(cfg->stages) * (static_cast<size_t>(cfg->stage_bytes) + 8);
         } else if (cfg->tma_ring == SL_RING_CTA) {
             if (cta > 992) return fail(SL_ERR_ARG, "TMA consumer threads %d > 992", cta);
             p->fn = sl::tma_kernel(dtype);

@@ -123,28 +123,28 @@ __global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
     cta_finish<DT>(acc, warp != 0, warp - 1, ncw, a, &cta_err);
 }
 
-// ---- k_tma_warp: one ring per warp (SL_RING_WARP) ----
-// Every warp owns a ring of nst stages of stage_bytes in dynamic shared memory
-// (warp w's ring after those of warps 0..w-1, then the CTA's full barriers,
-// one per stage per warp, count 1).  Its lane 0 is the ring's only producer
-// and its 32 lanes the only consumers, so a stage needs no empty barrier:
-// once the warp has read stage s (__syncwarp), lane 0 re-arms it with
-// arrive.expect_tx and issues the next cp.async.bulk into it.
+// ---- k_tma_warp: the CTA's stages dealt to its warps (SL_RING_WARP) ----
+// The CTA holds the same ring of stages x stage_bytes as k_tma, without a
+// producer warp: its W warps split the stages, warp w owning the nst =
+// stages / W consecutive stages after those of warps 0..w-1 (a sub-ring), and
+// the CTA's full barriers (one per stage, count 1) follow the stages in
+// dynamic shared memory.  A warp's lane 0 is its sub-ring's only producer and
+// its 32 lanes the only consumers, so a stage needs no empty barrier: once
+// the warp has read stage s (__syncwarp), lane 0 re-arms it with
+// arrive.expect_tx and issues the warp's next cp.async.bulk into it, after a
+// proxy fence that orders the lanes' generic-proxy reads of the stage before
+// the bulk copy's async-proxy writes.
 //
 // Chunks (stage-sized pieces of the buffer, the last one ragged) are dealt to
-// warps grid-wide: global warp g = blockIdx.x * W + w (W warps per CTA) takes
-// chunks g, g + G, g + 2G, ... over all passes (G = grid * W; chunk c reads
-// piece c mod nchunks, counted from the last piece for SL_DESC).  A warp's
-// j-th chunk lives in stage j mod nst and has landed when that stage's
-// barrier completes phase j / nst; the producer refills a stage only after
-// its warp has read it, so no barrier runs more than one phase ahead of its
-// waiter.  A full stage gives each lane stage_bytes/512 vectors (8 for 4 KiB),
-// read 8 at a time.
+// warps grid-wide: global warp g = blockIdx.x * W + w takes chunks g, g + G,
+// g + 2G, ... over all passes (G = grid * W; chunk c reads piece c mod
+// nchunks, counted from the last piece for SL_DESC).  A warp's j-th chunk
+// lives in its stage j mod nst and has landed when that stage's barrier
+// completes phase j / nst; lane 0 refills a stage only after its warp has
+// read it, so no barrier runs more than one phase ahead of its waiter.  A
+// full stage gives each lane stage_bytes/512 vectors (8 for 4 KiB), read 8
+// at a time.
 //
-// Waits are bounded as in k_tma: a timed-out wait records the error in the
-// CTA's error word, raises the abort flag (other warps stop at their next
-// wait) and the warp leaves its loop with all lanes together; lane 0 then
-// waits (bounded) for every copy it issued to land before the CTA exits.
 template <int DT, bool COV = false>
 __global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
     extern __shared__ __align__(128) uint8_t ring[];
@@ -152,18 +152,20 @@ __global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
     __shared__ uint32_t cta_err;
 
     cta_start(a);
-    const uint32_t nst = static_cast<uint32_t>(a.nst);
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const uint32_t nst = static_cast<uint32_t>(a.nst) / nw;  // stages of this warp (the host checks W | stages)
     const uint64_t nchunks = a.ntiles;
     const uint64_t total = a.total;
     const uint32_t stage_bytes = a.tile_vec * 16u;
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const uint64_t bytes = a.nvec * 16ull;
     const uint8_t* __restrict__ gbuf = static_cast<const uint8_t*>(a.buf);
     const uint32_t my_ring = smem_addr(ring) + warp * nst * stage_bytes;
-    const uint32_t my_full = smem_addr(ring) + nw * nst * stage_bytes + warp * nst * 8u;
+    const uint32_t my_full = smem_addr(ring) + static_cast<uint32_t>(a.nst) * stage_bytes + warp * nst * 8u;
     const uint64_t G = static_cast<uint64_t>(gridDim.x) * nw;
     const uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * nw + warp;
-    const bool skip_one = (a.debug & SL_DEBUG_TMA_SKIP_STAGE) && g0 == 0;  // debug: leave chunk 1 of warp 0 unarmed
+    // debug: global warp 0 leaves its first chunk unarmed (it has one whenever
+    // the buffer is not empty), so its first wait runs out
+    const bool skip_one = (a.debug & SL_DEBUG_TMA_SKIP_STAGE) && g0 == 0;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -186,7 +188,8 @@ __global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
     };
     uint32_t armed = 0;     // lane 0: bit s = stage s has had a copy issued
     uint32_t last_par = 0;  // lane 0: bit s = parity of the phase of stage s's last copy
-    const auto issue = [&](uint32_t s, uint32_t par, uint64_t c) {
+    const auto issue = [&](uint32_t s, uint32_t par, uint64_t c, uint32_t j) {
+        if (skip_one && j == 0) return;  // the warp's j-th chunk (debug only)
         uint64_t off;
         uint32_t len;
         piece(c, off, len);
@@ -202,8 +205,7 @@ __global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
         for (uint32_t j = 0; j < nst; ++j) {
             const uint64_t c = g0 + j * G;
             if (c >= total) break;
-            if (skip_one && j == 1) continue;
-            issue(j, 0u, c);
+            issue(j, 0u, c, j);
         }
     }
 
@@ -239,8 +241,9 @@ __global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
         }
         __syncwarp();  // every lane has read stage s
         if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const uint64_t cn = c + nst * G;
-            if (cn < total) issue(s, (r + 1) & 1u, cn);
+            if (cn < total) issue(s, (r + 1) & 1u, cn, (r + 1) * nst + s);
         }
         if (++s == nst) { s = 0; ++r; }
     }

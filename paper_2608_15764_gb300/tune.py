@@ -73,12 +73,12 @@ class Point:
     def offered(self) -> int:
         """Offered in-flight bytes per CTA (for tie-breaking)."""
         if self.mech == SL_TMA:
-            return self.stage_bytes * self.stages * (self.cta // 32 if self.ring == SL_RING_WARP else 1)
+            return self.stage_bytes * self.stages
         return self.k * self.cta * (32 if self.mech == SL_LDG32 else 16)
 
     def label(self) -> str:
         if self.mech == SL_TMA:
-            ring = " warp-rings" if self.ring == SL_RING_WARP else ""
+            ring = " per-warp stages" if self.ring == SL_RING_WARP else ""
             return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}{ring}"
         dyn = " dyn" if self.order == 2 else ""
         kd = "D" if self.mech == SL_CPASYNC else "K"
@@ -109,8 +109,8 @@ class Point:
 
 def parse_point(text: str) -> Point:
     """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta',
-    'tma:stage_bytes:stages:cta' (one ring per CTA) or 'tmaw:stage_bytes:stages[:cta]' (one ring per
-    warp; cta defaults to warp_ring_cta)."""
+    'tma:stage_bytes:stages:cta' (one ring per CTA, producer warp) or 'tmaw:stage_bytes:stages[:cta]'
+    (the CTA's stages dealt to its warps; cta defaults to warp_ring_cta)."""
     f = text.split(":")
     if f[0] == "tmaw":
         sb, n = int(f[1]), int(f[2])
@@ -128,17 +128,10 @@ def parse_point(text: str) -> Point:
     raise ValueError(f"bad point {text!r}")
 
 
-# shared memory a CTA may use (the GB300 opt-in limit is 227 KiB), less room
-# for the kernels' static shared memory
-SMEM_BUDGET = 227 * 1024 - 4096
-
-
-def warp_ring_cta(stage_bytes: int, stages: int, max_warps: int = 32) -> int:
-    """CTA size of a one-ring-per-warp TMA point: as many warps as fit one
-    CTA's shared memory (each warp holds stages x (stage_bytes + 8) bytes),
-    at least one warp."""
-    per_warp = stages * (stage_bytes + 8)
-    return 32 * max(1, min(max_warps, SMEM_BUDGET // per_warp))
+def warp_ring_cta(stage_bytes: int, stages: int) -> int:
+    """CTA size of a TMA point whose CTA ring is dealt to its warps: one warp
+    per stage (each warp owns one stage of stage_bytes)."""
+    return 32 * stages
 
 
 TMA_STAGE_BYTES = (4096, 16384, 65536)
@@ -148,8 +141,9 @@ TMA_STAGES = tuple(range(2, 9))
 def default_points(cta: int = 256) -> list[Point]:
     """The K-response catalogue: LDG K 1-16 (16 bytes, .cg), four .L2::256B
     points, the dynamic-chunk traversal, 32-byte loads, cp.async D 1-8, and
-    TMA stage sizes 4/16/64 KiB x 2-8 stages in both ring layouts (one ring
-    per CTA at `cta` consumer threads; one ring per warp at warp_ring_cta).
+    TMA stage sizes 4/16/64 KiB x 2-8 stages in both ring layouts (read by
+    all `cta` consumer threads; dealt to the warps, one stage per warp and,
+    for even stage counts, two).
     Points whose shared memory does not fit are kept and recorded as
     infeasible by measure()."""
     pts = [Point(SL_LDG, k=k, cta=cta) for k in range(1, 17)]
@@ -160,8 +154,9 @@ def default_points(cta: int = 256) -> list[Point]:
     pts += [Point(SL_LDG32, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in range(1, 9)]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n) for s in TMA_STAGE_BYTES for n in TMA_STAGES]
-    pts += [Point(SL_TMA, cta=warp_ring_cta(s, n), stage_bytes=s, stages=n, ring=SL_RING_WARP)
-            for s in TMA_STAGE_BYTES for n in TMA_STAGES]
+    pts += [Point(SL_TMA, cta=c, stage_bytes=s, stages=n, ring=SL_RING_WARP)
+            for s in TMA_STAGE_BYTES for n in TMA_STAGES
+            for c in ([32 * n, 16 * n] if n % 2 == 0 else [32 * n])]
     return pts
 
 

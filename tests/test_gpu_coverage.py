@@ -27,8 +27,8 @@ CONFIGS = [
     ("ldsts", dict(k=1, cta=256)), ("ldsts", dict(k=16, cta=256)),
     ("tma", dict(cta=256, stage_bytes=16384, stages=4)), ("tma", dict(cta=128, stage_bytes=4096, stages=2,
                                                                       order="desc")),
-    ("tma", dict(cta=224, stage_bytes=4096, stages=8, ring="warp")),
-    ("tma", dict(cta=64, stage_bytes=16384, stages=3, ring="warp", order="desc")),
+    ("tma", dict(cta=256, stage_bytes=4096, stages=8, ring="warp")),
+    ("tma", dict(cta=64, stage_bytes=16384, stages=4, ring="warp", order="desc")),
 ]
 
 
@@ -69,7 +69,7 @@ def test_every_vector_read_exactly_passes_times(sl, data, mech, kw, passes):
 @pytest.mark.parametrize("mech,kw", [("ldg", dict(k=16, cta=256)), ("ldg", dict(k=12, cta=256, order="dyn")),
                                      ("ldg32", dict(k=8, cta=256, order="dyn")), ("cpasync", dict(k=16, cta=256)),
                                      ("tma", dict(cta=256, stage_bytes=4096, stages=3)),
-                                     ("tma", dict(cta=256, stage_bytes=4096, stages=3, ring="warp"))])
+                                     ("tma", dict(cta=256, stage_bytes=4096, stages=8, ring="warp"))])
 def test_small_and_ragged_coverage(sl, data, nvec, mech, kw):
     dev, host, counts = data
     counts.fill_(-1)

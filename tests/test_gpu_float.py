@@ -107,7 +107,7 @@ def test_tma_float(sl, payloads, dt, stage, stages):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("stage,stages,cta", [(4096, 8, 224), (4096, 2, 864), (16384, 3, 128), (65536, 2, 32)])
+@pytest.mark.parametrize("stage,stages,cta", [(4096, 8, 256), (4096, 2, 64), (16384, 3, 96), (65536, 2, 32)])
 def test_tma_warp_rings_float(sl, payloads, dt, stage, stages, cta):
     _check(sl, payloads[dt], dt, sl.config("tma", cta=cta, stage_bytes=stage, stages=stages, ring="warp"))
 

@@ -48,8 +48,8 @@ CONFIGS = [
     ("tma", dict(cta=256, stage_bytes=4096, stages=2)),
     ("tma", dict(cta=256, stage_bytes=16384, stages=4, order="desc")),
     ("tma", dict(cta=256, stage_bytes=65536, stages=3)),
-    ("tma", dict(cta=224, stage_bytes=4096, stages=8, ring="warp")),
-    ("tma", dict(cta=64, stage_bytes=16384, stages=3, ring="warp", order="desc")),
+    ("tma", dict(cta=256, stage_bytes=4096, stages=8, ring="warp")),
+    ("tma", dict(cta=64, stage_bytes=16384, stages=4, ring="warp", order="desc")),
 ]
 IDS = [f"{m}-" + "-".join(f"{k}{v}" for k, v in kw.items()) for m, kw in CONFIGS]
 
@@ -168,7 +168,7 @@ def bf16_groups(sl):
 GROUP_CONFIGS = [("ldg", dict(k=1, cta=128)), ("ldg", dict(k=8, cta=256)), ("ldg32", dict(k=2, cta=128)),
                  ("cpasync", dict(k=2, cta=128)), ("ldsts", dict(k=2, cta=128)),
                  ("tma", dict(cta=128, stage_bytes=4096, stages=2)),
-                 ("tma", dict(cta=128, stage_bytes=4096, stages=2, ring="warp"))]
+                 ("tma", dict(cta=64, stage_bytes=4096, stages=2, ring="warp"))]
 
 
 @pytest.mark.parametrize("mech,kw", GROUP_CONFIGS,

@@ -48,8 +48,8 @@ def _results(sl, out, n):
     ("ldg32", dict(k=6, cta=256, order="dyn"), 32),
     ("tma", dict(cta=256, stage_bytes=16384, stages=4), 16), ("tma", dict(cta=512, stage_bytes=65536, stages=2,
                                                                          order="desc"), 16),
-    ("tma", dict(cta=224, stage_bytes=4096, stages=8, ring="warp"), 16),
-    ("tma", dict(cta=96, stage_bytes=16384, stages=4, ring="warp", order="desc"), 16),
+    ("tma", dict(cta=256, stage_bytes=4096, stages=8, ring="warp"), 16),
+    ("tma", dict(cta=128, stage_bytes=16384, stages=4, ring="warp", order="desc"), 16),
 ])
 def test_steps_each_pass_matches_oracle(sl, data, mech, kw, loads):
     dev, _, want = data
@@ -180,7 +180,7 @@ def test_dynamic_steps_float_sums(sl):
         assert abs(r.fsum - ref) <= 2e-6 * abs(ref)
 
 
-@pytest.mark.parametrize("ring,cta,stage", [("cta", 256, 16384), ("warp", 224, 4096)])
+@pytest.mark.parametrize("ring,cta,stage", [("cta", 256, 16384), ("warp", 128, 4096)])
 def test_tma_steps_report_a_timeout_on_its_own_pass(sl, data, ring, cta, stage):
     """A TMA pass whose bounded wait gives up (debug flag: one stage never
     armed) reports SL_ERR_TIMEOUT in its own result, and the passes before and

@@ -110,42 +110,42 @@ def test_tma_shapes(sl, data, cta, grid):
 
 
 @pytest.mark.parametrize("stage", [4096, 16384, 65536])
-@pytest.mark.parametrize("stages", [2, 3, 5, 8])
+@pytest.mark.parametrize("stages", [2, 3, 4, 8])
 @pytest.mark.parametrize("order", ["asc", "desc"])
 def test_tma_warp_rings(sl, data, stage, stages, order):
-    """One TMA ring per warp, at the largest CTA that fits and at two warps."""
-    from paper_2608_15764_gb300 import tune
+    """The CTA's TMA stages dealt to its warps: one, two and all stages per
+    warp."""
     dev, _, want = data
-    for cta in (tune.warp_ring_cta(stage, stages), 64):
+    for cta in sorted({32 * stages, 32 * max(1, stages // 2) if stages % 2 == 0 else 32 * stages, 32}):
         cfg = sl.config("tma", cta=cta, stage_bytes=stage, stages=stages, order=order, ring="warp")
         try:
             sl.sl_plan(NBYTES, sl.SL_U32, cfg)
         except sl.SLError as e:
-            # only a ring set too large for one CTA's shared memory is refused
-            assert e.status == sl.SL_ERR_INFEASIBLE and (cta // 32) * stages * (stage + 8) > 200 * 1024
+            # only a ring too large for one CTA's shared memory is refused
+            assert e.status == sl.SL_ERR_INFEASIBLE and stages * (stage + 8) > 200 * 1024
             continue
         r = _check(sl, dev, NBYTES, want, cfg)
         assert r.cta == cta
 
 
-@pytest.mark.parametrize("cta,grid", [(32, 1), (96, 3), (864, 0), (1024, 5), (224, 10007)])
-def test_tma_warp_ring_shapes(sl, data, cta, grid):
+@pytest.mark.parametrize("cta,grid,stages", [(32, 1, 2), (96, 3, 6), (256, 0, 8), (64, 10007, 4), (128, 0, 8)])
+def test_tma_warp_ring_shapes(sl, data, cta, grid, stages):
     dev, _, want = data
-    stages = 2 if cta <= 864 else 1
-    if stages < 2:  # 32 warps x 2 x 4 KiB exceeds one CTA's shared memory
-        with pytest.raises(sl.SLError) as e:
-            sl.sl_run(dev, dtype=sl.SL_U32, cfg=sl.config("tma", cta=cta, grid=grid, stage_bytes=4096, stages=2,
-                                                          ring="warp"))
-        assert e.value.status == sl.SL_ERR_INFEASIBLE
-        return
     r = _check(sl, dev, NBYTES, want, sl.config("tma", cta=cta, grid=grid, stage_bytes=4096, stages=stages,
                                                 ring="warp"))
     assert r.grid == (grid or r.grid)
 
 
+def test_tma_warp_ring_needs_warps_dividing_stages(sl, data):
+    dev, _, _ = data
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_run(dev, dtype=sl.SL_U32, cfg=sl.config("tma", cta=96, stage_bytes=4096, stages=4, ring="warp"))
+    assert e.value.status == sl.SL_ERR_ARG
+
+
 @pytest.mark.parametrize("mech,kw", [("ldg", {"k": 2}), ("ldg", {"k": 13}), ("cpasync", {"k": 3}),
                                      ("tma", {"stage_bytes": 4096, "stages": 3}),
-                                     ("tma", {"stage_bytes": 4096, "stages": 3, "ring": "warp"})])
+                                     ("tma", {"stage_bytes": 4096, "stages": 8, "ring": "warp"})])
 @pytest.mark.parametrize("passes", [2, 3])
 def test_passes_closed_form(sl, data, mech, kw, passes):
     dev, _, (s, x) = data
@@ -156,7 +156,7 @@ def test_passes_closed_form(sl, data, mech, kw, passes):
 @pytest.mark.parametrize("nvec", [0, 1, 2, 3, 31, 33, 255, 257, 4096 + 5])
 @pytest.mark.parametrize("mech,kw", [("ldg", {"k": 1}), ("ldg", {"k": 16}), ("cpasync", {"k": 8}),
                                      ("tma", {"stage_bytes": 4096, "stages": 2}),
-                                     ("tma", {"stage_bytes": 4096, "stages": 4, "ring": "warp"}),
+                                     ("tma", {"stage_bytes": 4096, "stages": 8, "ring": "warp"}),
                                      ("tma", {"stage_bytes": 65536, "stages": 2, "ring": "warp", "cta": 32})])
 def test_small_and_ragged(sl, data, nvec, mech, kw):
     dev, host, _ = data
