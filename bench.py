@@ -162,16 +162,8 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the kernel sources: DRAM-traffic counters taken on another
-    version of the kernels are not reported."""
-    import hashlib
-    csrc = os.path.join(ROOT, "paper_2608_15764_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.startswith("k_") or name.endswith(".cuh") or name == "sl_internal.h":
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
-    return h.hexdigest()[:16]
+    from paper_2608_15764_gb300.build import kernel_source_hash as h
+    return h()
 
 
 def _traffic(label: str, nbytes: int):

@@ -450,15 +450,19 @@ void sl_batch_destroy(sl_batch* b);
  * flush, no debug flags) like sl_enqueue: asynchronous on cfg->stream, the
  * result written to the DEVICE pointer dev_out (8-byte aligned), computing
  * the same checksum, issued-load count and float sum as sl_run.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.  Its scratch (per-warp
- * partials, timestamps, the error word) is one fixed file-scope __device__
- * array of SL_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that loads the
- * library until the process exits.  Limit: at most SL_NOALLOC_MAX_CTAS CTAs
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (one
+ * 32-byte partial per CTA plus a 256-byte control block: the timing window,
+ * the finished-CTA counter and the error word) is one fixed file-scope
+ * __device__ array of SL_NOALLOC_SCRATCH_BYTES bytes, held by every GPU that
+ * loads the library until the process exits.  Limit: at most SL_NOALLOC_MAX_CTAS CTAs
  * per call; larger launches are rejected with SL_ERR_ARG and a message.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array,
+ * before any stream capture.  The address is kept per device together with
+ * the driver's id of the context it was looked up in, and looked up again by
+ * the first call after that context has been replaced (e.g. by
+ * cudaDeviceReset).  Every call on a device shares the one array,
  * which keeps the previous call's contents (the error word is cleared by each
  * call): calls whose work overlaps on the GPU (different streams, or other
  * threads) race and must be serialized by the caller. */

@@ -31,6 +31,18 @@ HEADERS = ["sl_internal.h", "sl_device.cuh", "sl_mbar.cuh", "k_ldg.cuh", "k_batc
            os.path.join("..", "..", "include", "streamload.h")]
 
 
+def kernel_source_hash() -> str:
+    """Hash of the kernel sources (csrc/k_*, *.cuh, sl_internal.h): counters
+    taken on another version of the kernels are not reported against these."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.startswith("k_") or name.endswith(".cuh") or name == "sl_internal.h":
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
 def _nvcc() -> str:
     for cand in [shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"]:
         if cand and os.path.exists(cand):

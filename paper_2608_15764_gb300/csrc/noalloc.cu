@@ -16,9 +16,14 @@
 // array until the process exits.  Host code never uses the array's name as an
 // address (on the host it is only a stand-in); it asks the runtime for the
 // device address with cudaGetSymbolAddress, once per device, with that device
-// current, and passes that pointer to the kernels.
+// current, and passes that pointer to the kernels.  The address belongs to
+// the device's context: the cache remembers which context it was looked up
+// in (by the driver's unique context id) and looks it up again once that
+// context has been replaced, e.g. after cudaDeviceReset.
 #include <cstdint>
 #include <mutex>
+
+#include <cuda.h>  // CUcontext / CUresult types only; the driver is reached through the runtime
 
 #include "sl_internal.h"
 
@@ -38,12 +43,44 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[SL_NOALLOC_SCRA
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mu;
 unsigned char* g_na_ptr[NA_MAX_DEVICES] = {};
+unsigned long long g_na_ctx[NA_MAX_DEVICES] = {};  // context id the address was looked up in
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// The driver's unique id of the calling thread's current context, or 0 if
+// there is none (or the driver cannot tell).  Ids are never reused within a
+// process, so a replaced context never matches an old id.
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        (void)cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 // Device address of g_noalloc_scratch on device `dev` (which must be
-// current), looked up once per device.
+// current): looked up once per device, and again if the device's context
+// has been replaced since (the old address belonged to the old context).
 int scratch_for(int dev, unsigned char** out) {
     std::lock_guard<std::mutex> g(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_na_ptr[dev] || (ctx != 0 && ctx != g_na_ctx[dev])) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -51,6 +88,7 @@ int scratch_for(int dev, unsigned char** out) {
             return sl::set_error(SL_ERR_CUDA, "cudaGetSymbolAddress of the fixed scratch failed");
         }
         g_na_ptr[dev] = static_cast<unsigned char*>(p);
+        g_na_ctx[dev] = current_ctx_id();  // the lookup made a context current if there was none
     }
     *out = g_na_ptr[dev];
     return SL_OK;

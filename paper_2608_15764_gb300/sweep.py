@@ -15,9 +15,10 @@ GPU and checked against the first cell's checksum):
        occupancy API allows fewer than r) x sweep order {asc, desc}.
   c3   4 GiB; same bytes through LDG K 1..16 (grid-stride tiles, and the
        dynamic contiguous-chunk traversal for K in {1,2,3,4,6,8,12,16}),
-       cp.async D 1..8 and TMA
-       stage {4,16,64} KiB x stages 2..8 (cells over the shared-memory limit
-       are recorded as infeasible).
+       cp.async D 1..8 and TMA stage {4,16,64} KiB x stages 2..8 in both ring
+       layouts (one ring per CTA read by 256 consumer threads; the stages dealt
+       to the warps, one per warp and, for even stage counts, two); cells over
+       the shared-memory limit are recorded as infeasible.
   c4   allocations 512 MiB, 1, 2, 4, 8, 16, 20 GiB; LDG K in {1,2,4,8,16}.
   cpratio  paper §4.3: cp.async against the matched ld.global -> st.shared
        kernel at equal offered groups G in {1,2,4,8,12,16} (cp.async depth D =
@@ -34,9 +35,9 @@ GPU and checked against the first cell's checksum):
        latency-bound and its time falls about K-fold at fixed work.
   primary  the paper's primary cell shape (§4.2: one CTA of 32 warps per SM,
        .cg, 16-byte loads), K in {1,2,4,8}, on 4 GiB.
-  ncu  a small case for counter captures (1 GiB, one launch per cell, no
-       warm-up): LDG K=2 and K=8 (256 threads, 4 x SMs), LDG K=4 and K=12
-       with the dynamic-chunk traversal, cp.async D=2, TMA 16 KiB x 2 stages.
+  ncu-point  one launch (no warm-up) of the point --point (tune.parse_point
+       notation) on a --gib buffer (default 1 GiB): the small case of every
+       counter capture, one kernel per ncu invocation.
   c2w  the residency grid of c2 at the other two load widths: 4-byte loads
        (K in {1,2,4,8,16}) and 32-byte loads (K in {1,2,3,4,6,8}); with c2
        it gives the paper's regime map over warps x width.
@@ -52,9 +53,8 @@ GPU and checked against the first cell's checksum):
        that wrap around a 512 MiB, 2, 4, 8 or 20 GiB allocation, at 132 CTAs
        (the paper's H100) and one CTA per GB300 SM, K in {1,2,4,8}; reports
        the issued counts (mismatch across K) and GB/s of the issued bytes.
-  ncu-fixed / ncu-fixed-large  one launch per cell of the fixed-iteration
-       control at 132 CTAs, K = 2 and 8, on 512 MiB and 2 GiB (any metrics) or
-       8 and 20 GiB (one-pass metrics only).
+  ncu-fixed  one launch per cell of the fixed-iteration control at 132 CTAs,
+       K = 2 and 8, on a 2 GiB allocation (two launches).
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
@@ -64,19 +64,27 @@ GPU and checked against the first cell's checksum):
   two  paper §4.4: two co-resident plain-load streams in one CTA per SM,
        stream A = 1/2/4/8/16 warps, stream B = 0..16 warps, K = 1, 2, 4;
        displacement of A's bandwidth by B.
-  ncu-primary  the primary cell shape (1,024 threads, one CTA per SM), K in
-       {1,2,4,8}, 1 GiB, one launch each: the paper's counter audit per K.
-  ncu-alloc  LDG K = 2 and 8 (256 threads, 4 x SMs) on 512 MiB ... 20 GiB, one
-       launch each: counters per allocation size (one-pass metrics only).
-  ncu-points  every candidate point of the benchmark (tune.default_points)
-       on 1 GiB, then LDG K=2 and K=8 on 512 MiB and 2 GiB (one launch each,
-       no warm-up): DRAM bytes per launch for the roofline, and the paper's
-       counter audit (§4.2) across allocation sizes.
+  ncu-primary  the primary cell shape (1,024 threads, one CTA per SM), K = 2
+       and 8 (the paper's endpoints), 1 GiB, one launch each: the paper's
+       counter audit (two launches).
+
+Counter captures stay small: one kernel, one to three launches, at most a
+few GiB on the device (every ncu-* configuration above).  Counters at larger
+allocations are not captured; the kernels' own issued-load counts give the
+bytes read at every size.
 
     python -m paper_2608_15764_gb300.sweep --config c2 --out runs.jsonl [--repeats 10]
 
 A rerun with the same --out skips cells already recorded (resume after an
 interrupted run).
+
+    python -m paper_2608_15764_gb300.sweep --traffic SPEC=CSV [SPEC=CSV ...] --traffic-out FILE
+
+writes the DRAM bytes per launch of each point (SPEC in tune.parse_point
+notation) from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
+--print-units base --csv` logs of single-launch `ncu-point` captures, with
+the kernel-source hash they were taken on; bench.py reads it for the
+roofline's traffic.
 """
 from __future__ import annotations
 
@@ -96,7 +104,7 @@ def decline(bw_k2: float, bw_k8: float) -> float:
     return 100.0 * (bw_k8 - bw_k2) / bw_k2
 
 
-def _cells(config: str, sms: int):
+def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
     """Yield (cell_key, cell dict) in ascending order."""
     if config == "c1":
         for k in (1, 2, 4, 8):
@@ -132,13 +140,12 @@ def _cells(config: str, sms: int):
             for grid in (132, sms):
                 for k in (1, 2, 4, 8):
                     yield dict(mech="ldg", k=k, cta=1024, grid=grid, target_loads=target, gib=gib)
-    elif config in ("ncu-fixed", "ncu-fixed-large"):
-        # counters of the fixed-iteration control at K = 2 and 8, 132 CTAs:
-        # small allocations (all metrics) or large ones (one-pass metrics)
+    elif config == "ncu-fixed":
+        # counters of the fixed-iteration control at K = 2 and 8, 132 CTAs, on
+        # a 2 GiB allocation (two launches)
         target = 16785 * (1 << 20) // 16
-        for gib in ((0.5, 2) if config == "ncu-fixed" else (8, 20)):
-            for k in (2, 8):
-                yield dict(mech="ldg", k=k, cta=1024, grid=132, target_loads=target, gib=gib)
+        for k in (2, 8):
+            yield dict(mech="ldg", k=k, cta=1024, grid=132, target_loads=target, gib=2)
     elif config == "c2w":
         for cta in (128, 256, 512):
             for r in range(1, 9):
@@ -159,6 +166,10 @@ def _cells(config: str, sms: int):
         for sb in (4096, 16384, 65536):
             for n in range(2, 9):
                 yield dict(mech="tma", stage_bytes=sb, stages=n, cta=256, grid=0, gib=4)
+        for sb in (4096, 16384, 65536):
+            for n in range(2, 9):
+                for cta in ([32 * n, 16 * n] if n % 2 == 0 else [32 * n]):
+                    yield dict(mech="tma", stage_bytes=sb, stages=n, cta=cta, ring="warp", grid=0, gib=4)
     elif config == "c4":
         for gib in (0.5, 1, 2, 4, 8, 16, 20):
             for k in (1, 2, 4, 8, 16):
@@ -189,35 +200,22 @@ def _cells(config: str, sms: int):
                 yield dict(mech="ldg4", k=k, cta=cta, grid=0, gib=4)
             for k in (1, 2, 4):
                 yield dict(mech="ldg", k=k, cta=cta, grid=0, gib=4)
-    elif config == "ncu-points":
-        from .tune import MECH_NAMES, default_points
-        for p in default_points():
-            if p.mech == 2:
-                yield dict(mech="tma", stage_bytes=p.stage_bytes, stages=p.stages, cta=p.cta, grid=0, gib=1)
-            else:
-                yield dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop,
-                           trav=p.order, gib=1)
-        for gib in (0.5, 2):
-            for k in (2, 8):
-                yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
+    elif config == "ncu-point":
+        # one launch of one point: the small case of a counter capture
+        from .tune import MECH_NAMES, parse_point
+        if not point:
+            raise ValueError("ncu-point needs --point")
+        p = parse_point(point)
+        if p.mech == 2:
+            yield dict(mech="tma", stage_bytes=p.stage_bytes, stages=p.stages, cta=p.cta, grid=0, gib=gib,
+                       ring="warp" if p.ring else "cta")
+        else:
+            yield dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop, trav=p.order, gib=gib)
     elif config == "ncu-primary":
         # the paper's primary cell shape (one 1,024-thread CTA per SM) on 1 GiB:
-        # its counter audit (§4.2) per K
-        for k in (1, 2, 4, 8):
+        # its counter audit (§4.2) at the endpoints K = 2 and 8
+        for k in (2, 8):
             yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=1)
-    elif config == "ncu-alloc":
-        # the allocation sweep's sizes at K = 2 and 8 (one launch each): DRAM
-        # bytes, L1->L2 sectors and L2 hit rate per size
-        for gib in (0.5, 1, 2, 4, 8, 16, 20):
-            for k in (2, 8):
-                yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
-    elif config == "ncu":
-        yield dict(mech="ldg", k=2, cta=256, grid=4 * sms, gib=1)
-        yield dict(mech="ldg", k=8, cta=256, grid=4 * sms, gib=1)
-        yield dict(mech="ldg", k=4, cta=256, grid=0, trav=2, gib=1)
-        yield dict(mech="ldg", k=12, cta=256, grid=0, trav=2, gib=1)
-        yield dict(mech="cpasync", k=2, cta=256, grid=0, gib=1)
-        yield dict(mech="tma", stage_bytes=16384, stages=2, cta=256, grid=0, gib=1)
     else:
         raise ValueError(config)
 
@@ -238,7 +236,7 @@ def _key(cell: dict, order: str) -> str:
 
 
 def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"), verbose: bool = True,
-        warmup: int = 1):
+        warmup: int = 1, point: str | None = None, gib: float = 1.0, dtype: str = "u32"):
     import torch
 
     import paper_2608_15764_gb300 as sl
@@ -246,6 +244,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
     sl.load()
     info = sl.sl_device_info()
     sms = info["sm_count"]
+    dt = sl.DTYPES[dtype]
     done = set()
     if out and os.path.exists(out):
         for line in open(out):
@@ -255,7 +254,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                 continue
             if row.get("config") == config and "key" in row:
                 done.add(row["key"])
-    cells = list(_cells(config, sms))
+    cells = list(_cells(config, sms, point=point, gib=gib))
     rows = []
     by_size = {}
     for c in cells:
@@ -277,12 +276,13 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                 kw = dict(cta=c["cta"], grid=c["grid"], passes=passes, target_loads=c.get("target_loads", 0),
                           debug_flags=sl.SL_DEBUG_SMEM_SKEW(c.get("skew", 0)))
                 if c["mech"] == "tma":
-                    cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], **kw)
+                    cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], ring=c.get("ring", "cta"),
+                                    **kw)
                 else:
                     cfg = sl.config(c["mech"], k=c["k"], cop=c.get("cop", 0), order=c.get("trav", 0), **kw)
                 status, resident = 0, 0
                 try:
-                    plan = sl.sl_plan(nbytes, sl.SL_U32, cfg)
+                    plan = sl.sl_plan(nbytes, dt, cfg)
                     resident = plan.resident_per_sm
                     if c.get("resident_req") and resident < c["resident_req"]:
                         status = sl.SL_ERR_INFEASIBLE
@@ -299,7 +299,7 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
             if not cfgs:
                 continue
             # one sweep call per order: the cells run back to back in `seq` order
-            res = sl.sl_sweep(buf, cfgs, dtype=sl.SL_U32, repeats=repeats, warmup=warmup, sweep_order="asc")
+            res = sl.sl_sweep(buf, cfgs, dtype=dt, repeats=repeats, warmup=warmup, sweep_order="asc")
             for row, rr in zip(keep, res):
                 ok = [r for r in rr if r.status == 0]
                 fixed = row.get("target_loads", 0) > 0
@@ -598,15 +598,83 @@ def summarize(rows):
     return out
 
 
+def read_ncu_csv(path: str) -> list[dict]:
+    """Rows of an `ncu --csv --log-file` metrics log: one dict per (launch,
+    metric) with the kernel name, metric name, unit and value (thousands
+    separators removed)."""
+    import csv
+    with open(path) as f:
+        lines = f.read().splitlines()
+    start = next(i for i, l in enumerate(lines) if l.startswith('"ID"'))
+    rows = []
+    for r in csv.DictReader(lines[start:]):
+        v = r.get("Metric Value", "").replace(",", "")
+        try:
+            val = float(v)
+        except ValueError:
+            continue
+        rows.append({"id": int(r["ID"]), "kernel": r["Kernel Name"], "metric": r["Metric Name"],
+                     "unit": r.get("Metric Unit", ""), "value": val})
+    return rows
+
+
+def write_traffic(pairs: list[str], out: str, gib: float = 1.0) -> dict:
+    """profiles/traffic.json from single-launch captures: pairs 'SPEC=CSV'."""
+    from .build import kernel_source_hash
+    from .tune import parse_point
+    points = {}
+    for pair in pairs:
+        spec, path = pair.split("=", 1)
+        rows = read_ncu_csv(path)
+        ids = sorted({r["id"] for r in rows})
+        if len(ids) != 1:
+            raise ValueError(f"{path}: expected one captured launch, found {len(ids)}")
+        m = {r["metric"]: r for r in rows}
+        for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            if m[name]["unit"] not in ("byte", "bytes", "B"):
+                raise ValueError(f"{path}: {name} in {m[name]['unit']!r}; capture with --print-units base")
+        rd, wr = m["dram__bytes_read.sum"]["value"], m["dram__bytes_write.sum"]["value"]
+        points[parse_point(spec).label()] = {
+            "spec": spec, "kernel": m["dram__bytes_read.sum"]["kernel"], "bytes": int(gib * (1 << 30)),
+            "dram_read": int(rd), "dram_write": int(wr), "dram_bytes_per_launch": int(rd + wr)}
+    doc = {"kernel_source_hash": kernel_source_hash(),
+           "command": "for each point: python -m paper_2608_15764_gb300.sweep --config ncu-point --point SPEC "
+                      "--repeats 1 > plain.log && ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
+                      "--print-units base --clock-control none -k regex:\"k_(ldg|tma|cpasync)\" -c 1 --csv "
+                      "--log-file SPEC.csv python -m paper_2608_15764_gb300.sweep --config ncu-point --point SPEC "
+                      "--repeats 1",
+           "note": f"DRAM bytes per launch on a {gib:g} GiB buffer, one captured launch per point; bench.py scales "
+                   "them to its buffer by bytes read",
+           "points": points}
+    with open(out, "w") as f:
+        json.dump(doc, f, indent=1)
+    return doc
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--config", required=True,
-                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary", "ncu", "ncu-points", "ncu-primary", "ncu-alloc", "ncu-fixed", "ncu-fixed-large", "l2",
-                             "cpratio", "ladder", "k1gate", "two", "launches"])
+    ap.add_argument("--traffic", nargs="+", default=None, metavar="SPEC=CSV",
+                    help="write --traffic-out from single-launch ncu-point captures instead of running a sweep")
+    ap.add_argument("--traffic-out", default=os.path.join("profiles", "traffic.json"))
+    ap.add_argument("--config", required=False,
+                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary",
+                             "ncu-point", "ncu-primary", "ncu-fixed", "l2", "cpratio", "ladder", "k1gate", "two",
+                             "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
     ap.add_argument("--orders", default="asc,desc")
+    ap.add_argument("--point", default=None, help="ncu-point: the point, e.g. ldgdyn:2:512 or tmaw:4096:8:256")
+    ap.add_argument("--gib", type=float, default=1.0, help="ncu-point: buffer size in GiB")
+    ap.add_argument("--dtype", default="u32", choices=["u32", "f32", "bf16", "fp8"],
+                    help="fold of every cell (the buffer holds splitmix64 bits whatever the dtype: for float "
+                         "dtypes only timing and counters mean anything, the float sums do not)")
     a = ap.parse_args(argv)
+    if a.traffic:
+        doc = write_traffic(a.traffic, a.traffic_out, gib=a.gib)
+        print(json.dumps({"traffic_points": len(doc["points"]), "out": a.traffic_out}), flush=True)
+        return 0
+    if not a.config:
+        ap.error("--config is required")
     t0 = time.time()
     if a.config == "launches":
         run_launches(a.out, launches=a.repeats)
@@ -622,7 +690,8 @@ def main(argv=None):
         return 0
     ncu = a.config.startswith("ncu")
     orders = ("asc",) if ncu else tuple(a.orders.split(","))
-    rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if ncu else 1)
+    rows = run(a.config, a.out, repeats=a.repeats, orders=orders, warmup=0 if ncu else 1, point=a.point, gib=a.gib,
+               dtype=a.dtype)
     for s in summarize(rows):
         print(json.dumps({"summary": s}), flush=True)
     for s in cp_ratio(rows):

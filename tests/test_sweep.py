@@ -37,7 +37,10 @@ def test_cell_grids():
     assert sum(c["mech"] == "ldg" and not c.get("trav") for c in c3) == 16
     assert sum(c["mech"] == "ldg" and c.get("trav") == 2 for c in c3) == 8
     assert sum(c["mech"] == "cpasync" for c in c3) == 8
-    assert sum(c["mech"] == "tma" for c in c3) == 21
+    assert sum(c["mech"] == "tma" and c.get("ring", "cta") == "cta" for c in c3) == 21
+    # the stages dealt to the warps: one per warp at every count, two per warp at even counts
+    assert sum(c["mech"] == "tma" and c.get("ring") == "warp" for c in c3) == 3 * (7 + 4)
+    assert all(c["stages"] % (c["cta"] // 32) == 0 for c in c3 if c.get("ring") == "warp")
     c4 = list(sweep._cells("c4", sms))
     assert sorted({c["gib"] for c in c4}) == [0.5, 1, 2, 4, 8, 16, 20]
     prim = list(sweep._cells("primary", sms))
@@ -123,3 +126,18 @@ def test_tune_points_specs_loads_and_choice():
     a.step_gbs, b.step_gbs, c.step_gbs = [7500.0], [7400.0], []
     assert tune.choose([a, b, c]) is b          # within 0.5% of the best: fewer bytes in flight
     assert tune.choose([a, b, c], steps=True) is a
+
+
+def test_counter_capture_configs_stay_small():
+    """Every counter-capture configuration is one or two launches on at most
+    2 GiB (the capture-size rule for multi-pass ncu runs)."""
+    from paper_2608_15764_gb300 import sweep
+    sms = 152
+    for cfg, kw in [("ncu-primary", {}), ("ncu-fixed", {}), ("ncu-point", {"point": "ldgdyn:2:512"}),
+                    ("ncu-point", {"point": "tmaw:4096:8:256"}), ("ncu-point", {"point": "tma:65536:2:256"})]:
+        cells = list(sweep._cells(cfg, sms, **kw))
+        assert 1 <= len(cells) <= 2 and all(c["gib"] <= 2 for c in cells), cfg
+    w = list(sweep._cells("ncu-point", sms, point="tmaw:4096:8:256"))[0]
+    assert (w["mech"], w["ring"], w["stages"], w["cta"]) == ("tma", "warp", 8, 256)
+    with pytest.raises(ValueError):
+        list(sweep._cells("ncu-alloc", sms))
