@@ -55,6 +55,8 @@ GPU and checked against the first cell's checksum):
        the issued counts (mismatch across K) and GB/s of the issued bytes.
   ncu-fixed  one launch per cell of the fixed-iteration control at 132 CTAs,
        K = 2 and 8, on a 2 GiB allocation (two launches).
+  ncu-cpskew  cp.async D=4 at 256 threads with its shared-memory ring on a
+       128-byte boundary and 16 bytes past one, 1 GiB (two launches).
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
        (SL_LDG4) at K = 1 (the gate) and K up to 16, CTA 256 and 1024, on
        4 GiB, beside 16-byte LDG at K = 1, 2, 4.
@@ -211,6 +213,9 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
                        ring="warp" if p.ring else "cta")
         else:
             yield dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop, trav=p.order, gib=gib)
+    elif config == "ncu-cpskew":
+        for skew in (0, 1):
+            yield dict(mech="cpasync", k=4, cta=256, grid=0, skew=skew, gib=1)
     elif config == "ncu-primary":
         # the paper's primary cell shape (one 1,024-thread CTA per SM) on 1 GiB:
         # its counter audit (§4.2) at the endpoints K = 2 and 8
@@ -658,7 +663,7 @@ def main(argv=None):
     ap.add_argument("--traffic-out", default=os.path.join("profiles", "traffic.json"))
     ap.add_argument("--config", required=False,
                     choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary",
-                             "ncu-point", "ncu-primary", "ncu-fixed", "l2", "cpratio", "ladder", "k1gate", "two",
+                             "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "l2", "cpratio", "ladder", "k1gate", "two",
                              "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)

@@ -133,7 +133,7 @@ def test_counter_capture_configs_stay_small():
     2 GiB (the capture-size rule for multi-pass ncu runs)."""
     from paper_2608_15764_gb300 import sweep
     sms = 152
-    for cfg, kw in [("ncu-primary", {}), ("ncu-fixed", {}), ("ncu-point", {"point": "ldgdyn:2:512"}),
+    for cfg, kw in [("ncu-primary", {}), ("ncu-fixed", {}), ("ncu-cpskew", {}), ("ncu-point", {"point": "ldgdyn:2:512"}),
                     ("ncu-point", {"point": "tmaw:4096:8:256"}), ("ncu-point", {"point": "tma:65536:2:256"})]:
         cells = list(sweep._cells(cfg, sms, **kw))
         assert 1 <= len(cells) <= 2 and all(c["gib"] <= 2 for c in cells), cfg
