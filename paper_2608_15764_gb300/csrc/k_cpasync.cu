@@ -66,6 +66,23 @@ __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
         const uint32_t nrem = nbase < nvec ? static_cast<uint32_t>(min(nvec - nbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
         const bool cfull = cbase - threadIdx.x + tile_vec <= nvec;
         const uint4* np = buf + (has_next ? nbase : 0);
+        if (cfull && has_next && nbase - threadIdx.x + tile_vec <= nvec) {
+            // The current and the next tile are both whole (every tile but the
+            // last one or two of a pass): each chunk is folded and its slot
+            // refilled with no range checks, so a low depth pays less than a
+            // dozen instructions per 16-byte chunk.
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                cp_async_wait<D - 1>();
+                acc.fold(lds16(my0 + k * stride));
+                cp_async16(my0 + k * stride, np + static_cast<uint32_t>(k) * cta);
+                cov_count<COV>(a, (np + static_cast<uint32_t>(k) * cta) - buf);
+                cp_async_commit();
+            }
+            ++full_tiles;
+            continue;
+        }
+        // the last tiles: chunks past the buffer's end are neither folded nor copied
         uint32_t off = 0;  // k * cta
 #pragma unroll
         for (int k = 0; k < D; ++k) {

@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
 // full stage gives each lane stage_bytes/512 vectors (8 for 4 KiB), read 8
 // at a time.
 //
+// The warp count divides the stage count (at most SL_MAX_STAGES), so a CTA has
+// at most SL_MAX_STAGES warps; registers are capped for four such CTAs per SM.
 template <int DT, bool COV = false>
-__global__ void __launch_bounds__(1024, 1) k_tma_warp(const KArgs a) {
+__global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs a) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ volatile int abort_flag;
     __shared__ uint32_t cta_err;

@@ -1,0 +1,33 @@
+"""Host-side pieces of bench.py that need no GPU: the oracle's prefix
+checksums of the allocation sweep (against whole-buffer checksums) and the
+tile count behind the tuned per-buffer grids."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import oracle  # noqa: E402
+from paper_2608_15764_gb300 import workloads  # noqa: E402
+
+
+def test_prefix_checksums_match_whole_buffers():
+    piece = 16 << 20
+    sizes = [piece, 3 * piece]
+    cks, gbs, sec = bench.oracle_prefix_checksums(1, sizes, threads=4)
+    assert gbs > 0 and sec > 0
+    for s in sizes:
+        assert cks[s] == oracle.checksum(workloads.splitmix_u32(1, s // 4))
+    with pytest.raises(AssertionError):
+        bench.oracle_prefix_checksums(1, [piece + 16], threads=2)
+
+
+def test_tiles_per_mechanism():
+    import paper_2608_15764_gb300 as sl
+    assert bench._tiles(sl.config("ldg", k=4, cta=256), 16 * 1024) == 1
+    assert bench._tiles(sl.config("ldg", k=4, cta=256), 16 * 1025) == 2
+    assert bench._tiles(sl.config("cpasync", k=2, cta=128), 16 * 256 * 3) == 3
+    assert bench._tiles(sl.config("tma", stage_bytes=16384, stages=4), 16384 * 5 + 16) == 6

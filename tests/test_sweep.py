@@ -141,3 +141,34 @@ def test_counter_capture_configs_stay_small():
     assert (w["mech"], w["ring"], w["stages"], w["cta"]) == ("tma", "warp", 8, 256)
     with pytest.raises(ValueError):
         list(sweep._cells("ncu-alloc", sms))
+
+
+def test_traffic_writer_reads_single_launch_captures(tmp_path):
+    """The ncu CSV reader and the traffic writer: base units, one launch per
+    capture, labels matching the benchmark's point labels."""
+    from paper_2608_15764_gb300 import sweep, tune
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+           '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+
+    def row(i, metric, unit, value):
+        return (f'"{i}","1","python","h","void sl::k_ldg_dyn<4, 256, 0, 0>(sl::KArgs)","1","7","(256, 1, 1)",'
+                f'"(912, 1, 1)","0","10.3","","{metric}","{unit}","{value}"')
+
+    good = tmp_path / "good.csv"
+    good.write_text("\n".join(["==PROF== Connected", hdr, row(0, "dram__bytes_read.sum", "byte", "1,073,770,000"),
+                               row(0, "dram__bytes_write.sum", "byte", "2,964,736")]) + "\n")
+    out = tmp_path / "traffic.json"
+    doc = sweep.write_traffic([f"ldgdyn:4:256={good}"], str(out))
+    e = doc["points"][tune.parse_point("ldgdyn:4:256").label()]
+    assert e["dram_read"] == 1073770000 and e["dram_bytes_per_launch"] == 1073770000 + 2964736
+    assert json.load(open(out))["kernel_source_hash"] == doc["kernel_source_hash"]
+    scaled = tmp_path / "scaled.csv"
+    scaled.write_text("\n".join([hdr, row(0, "dram__bytes_read.sum", "Gbyte", "1.07"),
+                                 row(0, "dram__bytes_write.sum", "Mbyte", "2.9")]) + "\n")
+    with pytest.raises(ValueError):
+        sweep.write_traffic([f"ldgdyn:4:256={scaled}"], str(out))
+    two = tmp_path / "two.csv"
+    two.write_text("\n".join([hdr, row(0, "dram__bytes_read.sum", "byte", "1"), row(0, "dram__bytes_write.sum", "byte", "1"),
+                              row(1, "dram__bytes_read.sum", "byte", "1"), row(1, "dram__bytes_write.sum", "byte", "1")]))
+    with pytest.raises(ValueError):
+        sweep.write_traffic([f"ldgdyn:4:256={two}"], str(out))
