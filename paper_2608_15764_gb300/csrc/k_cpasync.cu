@@ -53,24 +53,17 @@ __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
             cp_async_commit();
         }
     }
+    const uint32_t nwhole = static_cast<uint32_t>(nvec / tile_vec);  // whole tiles of a pass: 0 .. nwhole-1
 #pragma unroll 1
     while (c.it < total) {
         const uint32_t cur = c.tile(a);
         c.next(ntiles);
         const bool has_next = c.it < total;
-        const uint64_t cbase = static_cast<uint64_t>(cur) * tile_vec + threadIdx.x;
-        const uint64_t nbase = has_next ? static_cast<uint64_t>(c.tile(a)) * tile_vec + threadIdx.x : nvec;
-        // vectors left from this thread's first chunk of the current / next
-        // tile, clamped to 32 bits: chunk k is in range iff k*cta < rem
-        const uint32_t crem = cbase < nvec ? static_cast<uint32_t>(min(nvec - cbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
-        const uint32_t nrem = nbase < nvec ? static_cast<uint32_t>(min(nvec - nbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
-        const bool cfull = cbase - threadIdx.x + tile_vec <= nvec;
-        const uint4* np = buf + (has_next ? nbase : 0);
-        if (cfull && has_next && nbase - threadIdx.x + tile_vec <= nvec) {
+        if (cur < nwhole && has_next && c.tile(a) < nwhole) {
             // The current and the next tile are both whole (every tile but the
             // last one or two of a pass): each chunk is folded and its slot
-            // refilled with no range checks, so a low depth pays less than a
-            // dozen instructions per 16-byte chunk.
+            // refilled with no range checks and no 64-bit bookkeeping.
+            const uint4* np = buf + static_cast<uint64_t>(c.tile(a)) * tile_vec + threadIdx.x;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 cp_async_wait<D - 1>();
@@ -82,6 +75,14 @@ __global__ void __launch_bounds__(D > 8 ? 512 : 1024) k_cpasync(const KArgs a) {
             ++full_tiles;
             continue;
         }
+        const uint64_t cbase = static_cast<uint64_t>(cur) * tile_vec + threadIdx.x;
+        const uint64_t nbase = has_next ? static_cast<uint64_t>(c.tile(a)) * tile_vec + threadIdx.x : nvec;
+        // vectors left from this thread's first chunk of the current / next
+        // tile, clamped to 32 bits: chunk k is in range iff k*cta < rem
+        const uint32_t crem = cbase < nvec ? static_cast<uint32_t>(min(nvec - cbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
+        const uint32_t nrem = nbase < nvec ? static_cast<uint32_t>(min(nvec - nbase, static_cast<uint64_t>(0xFFFFFFFFu))) : 0u;
+        const bool cfull = cur < nwhole;
+        const uint4* np = buf + (has_next ? nbase : 0);
         // the last tiles: chunks past the buffer's end are neither folded nor copied
         uint32_t off = 0;  // k * cta
 #pragma unroll
