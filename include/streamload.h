@@ -17,9 +17,10 @@
  *               groups in flight (paper §4.3 compares cp.async with plain
  *               loads).
  *   SL_TMA      Blackwell bulk-async copies (cp.async.bulk) of whole stages
- *               through an mbarrier ring (paper §2 names the TMA and bulk
- *               copies; the paper has no TMA kernel, the ring is this
- *               library's design).
+ *               through an mbarrier ring of `stages` stages per CTA, read by
+ *               all of the CTA's warps or dealt to them (sl_tma_ring) (paper
+ *               §2 names the TMA and bulk copies; the paper has no TMA
+ *               kernel, the rings are this library's design).
  *
  * and two layered forms: float payloads (FP32 / BF16 / FP8-E4M3) summed with
  * compensated FP32 accumulation (every addition's rounding error recovered
