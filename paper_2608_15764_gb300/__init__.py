@@ -84,8 +84,10 @@ def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *
            debug_flags: int = 0, host_direct: bool = False, target_loads: int = 0, ring="cta",
            stream=None) -> sl_config:
     """Build an sl_config.  mech: "ldg" / "cpasync" / "tma" (or the enum);
-    k: K for LDG, depth D for cp.async; stage_bytes/stages/ring ("cta": one
-    ring per CTA, "warp": one ring per warp) for TMA."""
+    k: K for LDG, depth D for cp.async; stage_bytes/stages/ring for TMA (ring
+    "cta": the CTA's stages read by all its consumer warps, filled by a
+    producer warp; "warp": the CTA's stages dealt to its warps, cta/32
+    dividing stages)."""
     c = sl_config()
     c.mech = MECHS[mech] if isinstance(mech, str) else int(mech)
     c.k = int(k)

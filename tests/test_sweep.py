@@ -114,8 +114,19 @@ def test_tune_points_specs_loads_and_choice():
     pts = tune.default_points()
     for p in pts:
         q = tune.parse_point(p.spec())
-        assert (q.mech, q.k, q.cta, q.order, q.stage_bytes, q.stages) == \
-            (p.mech, p.k, p.cta, p.order, p.stage_bytes, p.stages), p.spec()
+        assert (q.mech, q.k, q.cta, q.order, q.stage_bytes, q.stages, q.ring) == \
+            (p.mech, p.k, p.cta, p.order, p.stage_bytes, p.stages, p.ring), p.spec()
+    # the catalogue: LDG K 1-16, cp.async D 1-8, TMA 4/16/64 KiB x 2-8 in both ring layouts, every
+    # per-warp point with a warp count dividing its stage count
+    from paper_2608_15764_gb300 import SL_CPASYNC, SL_LDG, SL_RING_WARP, SL_TMA
+    assert sorted(q.k for q in pts if q.mech == SL_LDG and q.order == 0 and q.cop == 0) == list(range(1, 17))
+    assert sorted(q.k for q in pts if q.mech == SL_CPASYNC) == list(range(1, 9))
+    for ring in (0, SL_RING_WARP):
+        got = {(q.stage_bytes, q.stages) for q in pts if q.mech == SL_TMA and q.ring == ring}
+        assert got == {(s, n) for s in (4096, 16384, 65536) for n in range(2, 9)}
+    assert all(q.stages % (q.cta // 32) == 0 for q in pts if q.mech == SL_TMA and q.ring == SL_RING_WARP)
+    w = tune.parse_point("tmaw:4096:8")
+    assert (w.ring, w.cta, w.offered) == (SL_RING_WARP, 256, 8 * 4096) and "per-warp" in w.label()
     p = tune.parse_point("ldg32dyn:6:256")
     assert p.mech == SL_LDG32 and p.order == SL_DYN and p.overlapped
     assert p.cfg(grid=0).grid == 0 and p.cfg().order == SL_DYN and p.cfg(order="asc").order == 0
