@@ -194,6 +194,15 @@ def host_buffer(nbytes: int, pinned: bool):
     return t
 
 
+def _fractions(gbs) -> dict:
+    """A GB/s figure as fractions of the 8 TB/s datasheet and of the measured
+    copy peak (MEASURED_PEAKS.json, else the fallback)."""
+    if not gbs:
+        return {"frac_of_datasheet": None, "frac_of_measured_copy": None}
+    peak, _ = _peaks()
+    return {"frac_of_datasheet": round(gbs / DATASHEET_GBS, 4), "frac_of_measured_copy": round(gbs / peak, 4)}
+
+
 def _roofline_simple(achieved: float, note: str) -> dict:
     """The HBM roofline object for a workload line without per-kernel DRAM
     counters (traffic null)."""
@@ -443,7 +452,7 @@ def run_ours(a):
         "spread": spread,
         "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent),
                    "ranks_agree": bool(ranks_agree)},
-        "curves": [p.as_dict() for p in points],
+        "curves": [{**p.as_dict(), **_fractions(p.median)} for p in points],
         "device": {k: info[k] for k in ("name", "sm_count", "l2_bytes", "cc_major", "cc_minor")},
     }
     del buf, buf2, bufs, dev_out, spread_out
@@ -516,7 +525,8 @@ def alloc_section(a, info) -> dict:
                 per_k[k] = round(statistics.median(nb / r.device_ns for r in rr), 1)
                 ok = ok and all((r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*cks[nb], nb // 16, 0)
                                 for r in rr)
-            row[order] = {"gbs": per_k, "k2_to_k8": round((per_k[8] - per_k[2]) / per_k[2], 4),
+            row[order] = {"gbs": per_k, "frac_of_datasheet": {k: round(v / DATASHEET_GBS, 4) for k, v in per_k.items()},
+                          "k2_to_k8": round((per_k[8] - per_k[2]) / per_k[2], 4),
                           "above_datasheet": any(v > DATASHEET_GBS for v in per_k.values()), "parity": ok}
             all_ok = all_ok and ok
         rows.append(row)
@@ -602,6 +612,7 @@ def prec_section(a) -> dict:
             worst_all = max(worst_all, gated)
             all_ok = all_ok and ck_ok and gated <= 2e-6
             points.append({**c, "gbs_median": round(statistics.median(gbs), 1) if gbs else None,
+                           **_fractions(statistics.median(gbs) if gbs else None),
                            "rel_err": err / abs(ref) if ref else None, "err_over_abs_sum": err / absum,
                            "gated_err": gated, "checksum_ok": ck_ok, "deterministic": len(set(fs)) == 1})
         best = max(points, key=lambda p: p["gbs_median"] or 0)
