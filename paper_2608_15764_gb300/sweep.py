@@ -16,9 +16,10 @@ GPU and checked against the first cell's checksum):
   c3   4 GiB; same bytes through LDG K 1..16 (grid-stride tiles, and the
        dynamic contiguous-chunk traversal for K in {1,2,3,4,6,8,12,16}),
        cp.async D 1..8 and TMA stage {4,16,64} KiB x stages 2..8 in both ring
-       layouts (one ring per CTA read by 256 consumer threads; the stages dealt
-       to the warps, one per warp and, for even stage counts, two); cells over
-       the shared-memory limit are recorded as infeasible.
+       layouts (one ring per CTA read by 256 consumer threads, and by 128 for
+       4 KiB stages; the stages dealt to the warps, one per warp and, for even
+       stage counts, two); cells over the shared-memory limit are recorded as
+       infeasible.
   c4   allocations 512 MiB, 1, 2, 4, 8, 16, 20 GiB; LDG K in {1,2,4,8,16}.
   cpratio  paper §4.3: cp.async against the matched ld.global -> st.shared
        kernel at equal offered groups G in {1,2,4,8,12,16} (cp.async depth D =
@@ -168,6 +169,8 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
         for sb in (4096, 16384, 65536):
             for n in range(2, 9):
                 yield dict(mech="tma", stage_bytes=sb, stages=n, cta=256, grid=0, gib=4)
+        for n in range(2, 9):  # 4 KiB stages read by 128 consumer threads (two vectors per lane)
+            yield dict(mech="tma", stage_bytes=4096, stages=n, cta=128, grid=0, gib=4)
         for sb in (4096, 16384, 65536):
             for n in range(2, 9):
                 for cta in ([32 * n, 16 * n] if n % 2 == 0 else [32 * n]):

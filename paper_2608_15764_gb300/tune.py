@@ -142,8 +142,8 @@ def default_points(cta: int = 256) -> list[Point]:
     """The K-response catalogue: LDG K 1-16 (16 bytes, .cg), four .L2::256B
     points, the dynamic-chunk traversal, 32-byte loads, cp.async D 1-8, and
     TMA stage sizes 4/16/64 KiB x 2-8 stages in both ring layouts (read by
-    all `cta` consumer threads; dealt to the warps, one stage per warp and,
-    for even stage counts, two).
+    all `cta` consumer threads, and by 128 for 4 KiB stages; dealt to the
+    warps, one stage per warp and, for even stage counts, two).
     Points whose shared memory does not fit are kept and recorded as
     infeasible by measure()."""
     pts = [Point(SL_LDG, k=k, cta=cta) for k in range(1, 17)]
@@ -154,6 +154,9 @@ def default_points(cta: int = 256) -> list[Point]:
     pts += [Point(SL_LDG32, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in range(1, 9)]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n) for s in TMA_STAGE_BYTES for n in TMA_STAGES]
+    # with 4 KiB stages a 256-thread CTA gives each consumer lane a single
+    # 16-byte vector per stage; 128 consumer threads read two
+    pts += [Point(SL_TMA, cta=128, stage_bytes=4096, stages=n) for n in TMA_STAGES]
     pts += [Point(SL_TMA, cta=c, stage_bytes=s, stages=n, ring=SL_RING_WARP)
             for s in TMA_STAGE_BYTES for n in TMA_STAGES
             for c in ([32 * n, 16 * n] if n % 2 == 0 else [32 * n])]

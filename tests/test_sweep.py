@@ -37,7 +37,7 @@ def test_cell_grids():
     assert sum(c["mech"] == "ldg" and not c.get("trav") for c in c3) == 16
     assert sum(c["mech"] == "ldg" and c.get("trav") == 2 for c in c3) == 8
     assert sum(c["mech"] == "cpasync" for c in c3) == 8
-    assert sum(c["mech"] == "tma" and c.get("ring", "cta") == "cta" for c in c3) == 21
+    assert sum(c["mech"] == "tma" and c.get("ring", "cta") == "cta" for c in c3) == 21 + 7
     # the stages dealt to the warps: one per warp at every count, two per warp at even counts
     assert sum(c["mech"] == "tma" and c.get("ring") == "warp" for c in c3) == 3 * (7 + 4)
     assert all(c["stages"] % (c["cta"] // 32) == 0 for c in c3 if c.get("ring") == "warp")
