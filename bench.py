@@ -241,6 +241,17 @@ def cpu_oracle(words, seconds: float):
     return ck, passes * words.nbytes / el / 1e9, threads, passes, el
 
 
+def cpu_oracle_single_thread(words, nbytes: int = 512 << 20):
+    """GB/s of the oracle's checksum on one host thread over the first
+    nbytes of the workload (one warm pass, then one timed pass)."""
+    import oracle
+    part = words[: nbytes // 4]
+    oracle.checksum(part)
+    t0 = time.perf_counter()
+    oracle.checksum(part)
+    return part.nbytes / (time.perf_counter() - t0) / 1e9
+
+
 def run_reference(a):
     rank, world, _ = _dist()
     if rank != 0:
@@ -406,6 +417,7 @@ def run_ours(a):
     # ---- CPU oracle on the host cores (bounded sample) and parity
     words = host.numpy().view("uint32")
     oc, cpu_gbs, threads, passes, el = cpu_oracle(words, a.cpu_seconds)
+    cpu_1t = cpu_oracle_single_thread(words)
     parity = (res[0].sum_u32, res[0].xor_u64) == oc and (rh.sum_u32, rh.xor_u64) == oc and e2e_host_ok
     del host
 
@@ -442,7 +454,9 @@ def run_ours(a):
                              "timed passes)"},
         "cpu_baseline": {"value": round(cpu_gbs, 2), "unit": "GB/s", "cores": threads, "kind": "oracle",
                          "sample": f"{passes} full passes over the {nbytes >> 20} MiB host buffer "
-                                   f"({el:.1f} s wall, {threads} threads)"},
+                                   f"({el:.1f} s wall, {threads} threads)",
+                         "single_thread_gbs": round(cpu_1t, 2),
+                         "single_thread_sample": "one pass over the first 512 MiB on one host thread"},
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": sl.RESULT_BYTES,
                 "api": f"sl_run_host, pinned host buffer, {e2e_best['mode']} mode, {e2e_best['point']}",
