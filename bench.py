@@ -419,6 +419,11 @@ def run_ours(a):
     oc, cpu_gbs, threads, passes, el = cpu_oracle(words, a.cpu_seconds)
     cpu_1t = cpu_oracle_single_thread(words)
     parity = (res[0].sum_u32, res[0].xor_u64) == oc and (rh.sum_u32, rh.xor_u64) == oc and e2e_host_ok
+    # every result every measured curve point produced (single launches and
+    # back-to-back passes) against the oracle's checksum and load count
+    curve_ok = {id(p): bool(p.results) and p.results == {(*oc, p.loads(nbytes), 0)}
+                for p in points if p.status == 0 and p.gbs}
+    curves_ok = all(curve_ok.values())
     del host
 
     peak, peak_kind = _peaks()
@@ -465,8 +470,10 @@ def run_ours(a):
         "clocks": clk,
         "spread": spread,
         "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent),
-                   "ranks_agree": bool(ranks_agree)},
-        "curves": [{**p.as_dict(), **_fractions(p.median)} for p in points],
+                   "ranks_agree": bool(ranks_agree), "curve_points_match_oracle": bool(curves_ok),
+                   "curve_points_checked": len(curve_ok)},
+        "curves": [{**p.as_dict(), **_fractions(p.median),
+                    **({"checksum_ok": curve_ok[id(p)]} if id(p) in curve_ok else {})} for p in points],
         "device": {k: info[k] for k in ("name", "sm_count", "l2_bytes", "cc_major", "cc_minor")},
     }
     del buf, buf2, bufs, dev_out, spread_out
@@ -483,7 +490,7 @@ def run_ours(a):
             f.write(json.dumps(line) + "\n")
     if dist:
         dist.destroy_process_group()
-    return 0 if parity and consistent and extras_ok else 3
+    return 0 if parity and consistent and curves_ok and extras_ok else 3
 
 
 # ---- allocation-size sweep (config c4) -------------------------------------------

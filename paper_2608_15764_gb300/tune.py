@@ -37,6 +37,7 @@ class Point:
     status: int = SL_OK
     resident: int = 0
     grid_used: int = 0
+    results: set = field(default_factory=set)  # distinct (sum_u32, xor_u64, issued_loads, status) seen
 
     def cfg(self, **kw):
         """The point's sl_config; keyword arguments override its fields."""
@@ -180,6 +181,7 @@ def measure(buf, nbytes: int, points: list[Point], dtype: int = SL_U32, repeats:
     rows = sl_sweep(buf, [p.cfg(flush_l2=flush_l2) for p in feasible], nbytes=nbytes, dtype=dtype,
                     repeats=repeats, warmup=warmup, sweep_order=sweep_order)
     for p, row in zip(feasible, rows):
+        p.results.update((r.sum_u32, r.xor_u64, r.issued_loads, r.status) for r in row)
         p.status = next((r.status for r in row if r.status != SL_OK), SL_OK)
         p.gbs = [nbytes / r.device_ns for r in row if r.status == SL_OK and r.device_ns]
         p.window_gbs = [nbytes / r.window_ns for r in row if r.status == SL_OK and r.window_ns]
@@ -192,10 +194,11 @@ def measure_steps(bufs, nbytes: int, points: list[Point], steps: int = 8, repeat
     pass i reading bufs[i % len(bufs)]: one sl_enqueue_steps call
     (overlapped passes, one full wave of CTAs) where the point allows it, else
     `steps` sl_enqueue calls; CUDA events on the current stream around the
-    passes, after one untimed round; median of `repeats` into step_gbs."""
+    passes, after one untimed round; median of `repeats` into step_gbs.  The
+    passes' results of the last repeat join the point's `results`."""
     import torch
 
-    from . import RESULT_BYTES, sl_enqueue, sl_enqueue_steps
+    from . import RESULT_BYTES, sl_enqueue, sl_enqueue_steps, sl_result
     bufs = list(bufs) if isinstance(bufs, (list, tuple)) else [bufs]
     out = torch.zeros(steps * RESULT_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -220,6 +223,10 @@ def measure_steps(bufs, nbytes: int, points: list[Point], steps: int = 8, repeat
             e1.record(stream)
             torch.cuda.synchronize()
             p.step_gbs.append(nbytes * steps / (e0.elapsed_time(e1) * 1e6))
+        raw = out.cpu().numpy().tobytes()
+        for i in range(steps):
+            r = sl_result.from_buffer_copy(raw[i * RESULT_BYTES:(i + 1) * RESULT_BYTES])
+            p.results.add((r.sum_u32, r.xor_u64, r.issued_loads, r.status))
     return points
 
 
