@@ -70,7 +70,7 @@ __device__ __forceinline__ void warp_item_store(const Acc<DT>& acc, WarpPartial*
 // loads per thread per tile (same fold and tile layout as k_ldg), guarded
 // ragged tail.
 template <int K, int CTA, int DT>
-__global__ void __launch_bounds__(CTA, 1) kb_ldg(const BArgs a) {
+__global__ void __launch_bounds__(CTA, ldg_min_blocks<K, CTA, DT>()) kb_ldg(const BArgs a) {
     __shared__ uint32_t slot;
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     for (;;) {

@@ -18,11 +18,12 @@
 namespace sl {
 
 template <int K, int CTA, int DT, int COP, bool COV = false>
-__global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
+__global__ void __launch_bounds__(CTA, ldg_min_blocks<K, CTA, DT>()) k_ldg(const KArgs a) {
     // launch_bounds(CTA, 1) lets ptxas keep all K loaded vectors in registers
     // (4K registers) instead of interleaving loads with folds to save
-    // registers; configurations whose kernel would spill are rejected on the
-    // host (local memory > 0), as the paper requires zero spills (§3).
+    // registers (bfloat16 folds at K <= 8: see ldg_min_blocks); configurations
+    // whose kernel would spill are rejected on the host (local memory > 0), as
+    // the paper requires zero spills (§3).
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     cta_start(a);
     const uint4* __restrict__ buf = static_cast<const uint4*>(a.buf);
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(CTA, 1) k_ldg(const KArgs a) {
 // bit-reproducible between runs, since a CTA's partial covers whichever
 // chunks it claimed.
 template <int K, int CTA, int DT, bool COV = false>
-__global__ void __launch_bounds__(CTA, 1) k_ldg_dyn(const KArgs a) {
+__global__ void __launch_bounds__(CTA, ldg_min_blocks<K, CTA, DT>()) k_ldg_dyn(const KArgs a) {
     constexpr uint32_t TILE = static_cast<uint32_t>(CTA) * K;
     __shared__ uint32_t slot[2];
     cta_start(a);

@@ -93,6 +93,20 @@ __device__ __forceinline__ float fp8_word_sum(uint32_t w, float acc) {
     return acc;
 }
 
+// ---- register budget of the plain-load kernels --------------------------------
+// Minimum resident CTAs per SM asked of the compiler for an LDG kernel
+// (__launch_bounds__).  A bfloat16 fold (eight TwoSum steps per vector) with
+// up to K = 8 loads in flight is held to 64 registers per thread, so that four
+// 256-thread (two 512-thread) CTAs stay resident: with fewer warps its
+// dependent TwoSum chains cannot hide the load latency (at K = 8 the
+// unconstrained allocation of 78 registers leaves three CTAs and ~7% less
+// bandwidth).  Every other kernel takes the registers it wants (K loaded
+// vectors must stay in registers).
+template <int K, int CTA, int DT>
+constexpr int ldg_min_blocks() {
+    return (DT == SL_BF16 && K <= 8 && CTA >= 256) ? 1024 / CTA : 1;
+}
+
 // ---- coverage audit ------------------------------------------------------------
 // In the coverage instantiations (COV = true) every load of 16-byte vector i
 // also adds 1 to a.cov[i]; elsewhere this compiles to nothing.
