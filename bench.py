@@ -472,8 +472,9 @@ def run_ours(a):
         "parity": {"oracle_match": bool(parity), "steps_consistent": bool(consistent),
                    "ranks_agree": bool(ranks_agree), "curve_points_match_oracle": bool(curves_ok),
                    "curve_points_checked": len(curve_ok)},
-        "curves": [{**p.as_dict(), **_fractions(p.median),
-                    **({"checksum_ok": curve_ok[id(p)]} if id(p) in curve_ok else {})} for p in points],
+        "curves": [{**{k: v for k, v in p.as_dict().items() if k not in ("gbs", "steps_overlapped")},
+                    **_fractions(p.median), **({"checksum_ok": curve_ok[id(p)]} if id(p) in curve_ok else {})}
+                   for p in points],
         "device": {k: info[k] for k in ("name", "sm_count", "l2_bytes", "cc_major", "cc_minor")},
     }
     del buf, buf2, bufs, dev_out, spread_out
@@ -634,8 +635,9 @@ def prec_section(a) -> dict:
             all_ok = all_ok and ck_ok and gated <= 2e-6
             points.append({**c, "gbs_median": round(statistics.median(gbs), 1) if gbs else None,
                            **_fractions(statistics.median(gbs) if gbs else None),
-                           "rel_err": err / abs(ref) if ref else None, "err_over_abs_sum": err / absum,
-                           "gated_err": gated, "checksum_ok": ck_ok, "deterministic": len(set(fs)) == 1})
+                           "rel_err": float(f"{err / abs(ref):.3g}") if ref else None,
+                           "err_over_abs_sum": float(f"{err / absum:.3g}"), "gated_err": float(f"{gated:.3g}"),
+                           "checksum_ok": ck_ok, "deterministic": len(set(fs)) == 1})
         best = max(points, key=lambda p: p["gbs_median"] or 0)
         per.append({"payload": name, "bytes": nbytes, "ref_fsum": ref, "abs_sum": absum,
                     "gate": "sum|x|" if small else "|sum|", "best": best, "points": points,
