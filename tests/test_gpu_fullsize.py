@@ -136,3 +136,38 @@ def test_allocation_sweep_largest_size(sl):
             assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, nbytes // 16), (k, order)
     del dev
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("payload", ["f32", "bf16", "fp8", "bf16-cancel"])
+def test_precision_full_size(sl, payload):
+    """The precision form at the benchmark's size (4 GiB per payload) through
+    the points it most often picks (LDG dynamic chunks K=8, cp.async D=6, TMA
+    with 4 KiB stages dealt to the warps, LDG K=8 grid-stride): raw-word
+    checksums bit-exact, float sums within 2e-6 of the oracle's FP64 sum of
+    the whole payload (computed on the host threads)."""
+    import math
+    from paper_2608_15764_gb300 import workloads as wl
+    nbytes = 4 << 30
+    if payload == "bf16-cancel":
+        dt, host = wl.BF16, wl.bf16_cancel(nbytes // 16)
+    else:
+        dt = {"f32": wl.F32, "bf16": wl.BF16, "fp8": wl.FP8_E4M3}[payload]
+        host = wl.payload(dt, nbytes // wl.ELEM_BYTES[dt])
+    n = host.size
+    t = os.cpu_count() or 1
+    cut = [i * (n // t) // 16 * 16 for i in range(t)] + [n]
+    with ThreadPoolExecutor(t) as ex:
+        parts = list(ex.map(lambda i: oracle.fsum(dt, host[cut[i]:cut[i + 1]]), range(t)))
+    ref, absum = math.fsum(p[0] for p in parts), math.fsum(p[1] for p in parts)
+    if payload == "bf16-cancel":
+        assert ref == (nbytes // 16) * (1 + 2.0 ** -5)
+    want = _oracle_parallel(host.view(np.uint32))
+    dev = torch.from_numpy(host.view(np.uint8)).cuda()
+    gate = 2e-6 * (absum if abs(ref) < 1e-3 * absum / math.sqrt(n) else abs(ref))
+    for cfg in [sl.config("ldg", k=8, cta=256, order="dyn"), sl.config("cpasync", k=6, cta=256),
+                sl.config("tma", cta=256, stage_bytes=4096, stages=8, ring="warp"), sl.config("ldg", k=8, cta=256)]:
+        r = sl.sl_run(dev, dtype=dt, cfg=cfg)
+        assert (r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*want, nbytes // 16, 0)
+        assert abs(r.fsum - ref) <= gate, (payload, r.fsum, ref)
+    del dev
+    torch.cuda.empty_cache()
