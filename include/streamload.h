@@ -102,7 +102,7 @@ typedef struct sl_config {
     int32_t mech;        /* sl_mech */
     int32_t k;           /* SL_LDG: K = independent 16-byte loads per thread per
                             iteration, 1..16.  SL_CPASYNC: D = commit groups in
-                            flight per thread, 1..16.  SL_LDSTS: G = loads per
+                            flight per thread, 1..16 (of `copies` each).  SL_LDSTS: G = loads per
                             thread staged through shared memory, 1..16.
                             SL_LDG4 / SL_LDG32: K loads of 4 / 32 bytes.
                             SL_TMA: ignored. */
@@ -130,7 +130,13 @@ typedef struct sl_config {
                             memory, or pageable memory where the device can
                             address it), with no staging copies */
     int32_t tma_ring;    /* SL_TMA only: sl_tma_ring, how the stages are shared */
-    int32_t reserved;    /* 0 */
+    int32_t copies;      /* SL_CPASYNC only: G = 16-byte copies a thread puts in
+                            each commit group, 1 (0 means 1; the paper's cell),
+                            2, 4 or 8, with D x G <= 16.  A tile is cta*D*G
+                            vectors; a thread keeps D*G*16 bytes in flight and
+                            pays one commit and one wait per G copies.  Other
+                            mechanisms and the batched form: 0 or 1
+                            (SL_ERR_ARG otherwise). */
     uint64_t target_loads; /* 0 (default): exact fixed work, every vector read
                             once per pass.  > 0: the paper's fixed-iteration
                             control (§3 "Fixed-work control"): every thread runs

@@ -82,12 +82,13 @@ def _stream_handle(stream):
 def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *, stage_bytes: int = 16384,
            stages: int = 4, flush_l2: bool = False, passes: int = 1, cop: int = SL_COP_CG,
            debug_flags: int = 0, host_direct: bool = False, target_loads: int = 0, ring="cta",
-           stream=None) -> sl_config:
+           copies: int = 1, stream=None) -> sl_config:
     """Build an sl_config.  mech: "ldg" / "cpasync" / "tma" (or the enum);
-    k: K for LDG, depth D for cp.async; stage_bytes/stages/ring for TMA (ring
-    "cta": the CTA's stages read by all its consumer warps, filled by a
-    producer warp; "warp": the CTA's stages dealt to its warps, cta/32
-    dividing stages)."""
+    k: K for LDG, depth D for cp.async; copies: G, the 16-byte copies per
+    cp.async commit group (1, 2, 4 or 8, D*G <= 16); stage_bytes/stages/ring
+    for TMA (ring "cta": the CTA's stages read by all its consumer warps,
+    filled by a producer warp; "warp": the CTA's stages dealt to its warps,
+    cta/32 dividing stages)."""
     c = sl_config()
     c.mech = MECHS[mech] if isinstance(mech, str) else int(mech)
     c.k = int(k)
@@ -103,6 +104,7 @@ def config(mech="ldg", k: int = 2, cta: int = 256, grid: int = 0, order="asc", *
     c.host_direct = int(bool(host_direct))
     c.target_loads = int(target_loads)
     c.tma_ring = RINGS[ring] if isinstance(ring, str) else int(ring)
+    c.copies = int(copies)
     c.stream = _stream_handle(stream)
     return c
 

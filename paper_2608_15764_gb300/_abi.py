@@ -54,7 +54,7 @@ class sl_config(ctypes.Structure):
         ("debug_flags", ctypes.c_int32),
         ("host_direct", ctypes.c_int32),
         ("tma_ring", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("copies", ctypes.c_int32),
         ("target_loads", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
     ]

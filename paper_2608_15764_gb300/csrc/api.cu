@@ -214,6 +214,9 @@ int occupancy(DevCtx* c, const void* fn, int block, size_t smem, int* out) {
     return SL_OK;
 }
 
+// G, the 16-byte copies per commit group of SL_CPASYNC (0 in the config means 1).
+int copies_per_group(const sl_config* cfg) { return cfg->copies == 0 ? 1 : cfg->copies; }
+
 int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, Plan* p) {
     if (!cfg) return fail(SL_ERR_ARG, "cfg is NULL");
     if (dtype < SL_U32 || dtype > SL_FP8_E4M3) return fail(SL_ERR_ARG, "bad dtype %d", dtype);
@@ -223,6 +226,8 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     if (cfg->passes < 0) return fail(SL_ERR_ARG, "passes %d < 0", cfg->passes);
     if (cfg->order != SL_ASC && cfg->order != SL_DESC && cfg->order != SL_DYN)
         return fail(SL_ERR_ARG, "bad order %d", cfg->order);
+    if (cfg->mech != SL_CPASYNC && cfg->copies != 0 && cfg->copies != 1)
+        return fail(SL_ERR_ARG, "copies per commit group (%d) applies to SL_CPASYNC only", cfg->copies);
     const bool dyn = cfg->order == SL_DYN;
     const bool fixed = cfg->target_loads > 0;
     if (fixed && cfg->mech != SL_LDG) return fail(SL_ERR_ARG, "the fixed-iteration control is implemented for SL_LDG");
@@ -295,17 +300,23 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
         p->warps = cta / 32;
         break;
     case SL_CPASYNC:
-    case SL_LDSTS:
+    case SL_LDSTS: {
         if (cfg->k < 1 || cfg->k > SL_MAX_D)
             return fail(SL_ERR_ARG, "%s depth %d not in 1..%d", cfg->mech == SL_CPASYNC ? "cp.async" : "ld/st.shared",
                         cfg->k, SL_MAX_D);
-        p->fn = cfg->mech == SL_CPASYNC ? sl::cpasync_kernel(dtype, cfg->k) : sl::ldsts_kernel(dtype, cfg->k);
+        const int g = copies_per_group(cfg);
+        if (g != 1 && g != 2 && g != 4 && g != 8)
+            return fail(SL_ERR_ARG, "cp.async copies per commit group %d not in {1, 2, 4, 8}", g);
+        if (cfg->k * g > SL_MAX_D)
+            return fail(SL_ERR_ARG, "cp.async D x G = %d x %d copies in flight exceeds %d", cfg->k, g, SL_MAX_D);
+        p->fn = cfg->mech == SL_CPASYNC ? sl::cpasync_kernel(dtype, cfg->k, g) : sl::ldsts_kernel(dtype, cfg->k);
         p->block = cta;
-        p->smem = static_cast<size_t>(cfg->k) * cta * 16 +
+        p->smem = static_cast<size_t>(cfg->k) * g * cta * 16 +
                   (((cfg->debug_flags >> SL_DEBUG_SMEM_SKEW_SHIFT) & 7) ? 128 : 0);  // room for a skewed ring
-        tile_vec = static_cast<uint64_t>(cta) * cfg->k;
+        tile_vec = static_cast<uint64_t>(cta) * cfg->k * g;
         p->warps = cta / 32;
         break;
+    }
     case SL_TMA:
         if (cfg->stage_bytes != 4096 && cfg->stage_bytes != 16384 && cfg->stage_bytes != 65536)
             return fail(SL_ERR_INFEASIBLE, "TMA stage size %d not 4096/16384/65536", cfg->stage_bytes);
@@ -438,7 +449,7 @@ const void* coverage_fn(const sl_config* cfg) {
         if (cfg->target_loads) return sl::ldg_fixed_cov_kernel(cfg->k, cfg->cta);
         return cfg->cop == SL_COP_CG ? sl::ldg_cov_kernel(cfg->k, cfg->cta, dyn) : nullptr;
     case SL_LDG32: return sl::ldg32_cov_kernel(cfg->k, cfg->cta, dyn);
-    case SL_CPASYNC: return sl::cpasync_cov_kernel(cfg->k);
+    case SL_CPASYNC: return sl::cpasync_cov_kernel(cfg->k, copies_per_group(cfg));
     case SL_LDSTS: return sl::ldsts_cov_kernel(cfg->k);
     case SL_TMA: return cfg->tma_ring == SL_RING_WARP ? sl::tma_warp_cov_kernel() : sl::tma_cov_kernel();
     default: return nullptr;
@@ -457,7 +468,7 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
         if (!fn)
             return fail(SL_ERR_ARG, "no coverage instantiation for this configuration (uint32; LDG K 1/3/8/16 "
                         "grid-stride or 2/12 SL_DYN at cta 128/256/512; SL_LDG32 K 1/3/8 at cta 256; "
-                        "fixed-iteration K 2/8 at cta 256/1024; cp.async D 1/4/16; SL_LDSTS G 1/16; TMA)");
+                        "fixed-iteration K 2/8 at cta 256/1024; cp.async D 1/4/16, D x G 2 x 4 and 3 x 2; SL_LDSTS G 1/16; TMA)");
         FuncInfo* fi = nullptr;
         rc = func_info(c, fn, p.smem, &fi);
         if (rc) return rc;

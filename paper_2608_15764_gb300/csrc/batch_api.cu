@@ -108,6 +108,9 @@ int plan_group(Group& g, int sms, int smem_optin) {
     const sl_config& c = g.cfg;
     if (c.cta < 32 || c.cta > 1024 || (c.cta & 31)) return bfail(SL_ERR_ARG, "tuning entry: bad cta");
     if (c.target_loads) return bfail(SL_ERR_ARG, "tuning entry: the batched form runs exact fixed work (target_loads 0)");
+    if (c.copies != 0 && c.copies != 1)
+        return bfail(SL_ERR_ARG, "tuning entry: the batched cp.async class kernel puts one copy in each commit "
+                     "group (copies must be 0 or 1)");
     switch (c.mech) {
     case SL_LDG:
         g.fn = sl::batch_ldg_kernel(g.dtype, c.k, c.cta);

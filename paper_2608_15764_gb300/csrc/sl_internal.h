@@ -27,7 +27,7 @@ struct KArgs {
     uint64_t nvec;          // 16-byte vectors in the buffer
     uint64_t ntiles;        // tiles per pass
     uint64_t total;         // tiles over all passes = ntiles * passes
-    uint32_t tile_vec;      // 16-byte vectors per tile (LDG: cta*K, CPASYNC: cta*D,
+    uint32_t tile_vec;      // 16-byte vectors per tile (LDG: cta*K, CPASYNC: cta*D*G,
                             // TMA: stage_bytes/16)
     int32_t desc;           // 1: walk tiles from the last one downward
     int32_t nst;            // TMA: ring stages (per CTA or per warp)
@@ -55,7 +55,7 @@ enum : uint32_t { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT_FULL = 1, DEV_ERR_TIMEOUT_EM
 // instantiation, or nullptr when out of range.  All take (KArgs).
 const void* ldg_kernel(int dtype, int k, int cta, int cop);
 const void* ldg_dyn_kernel(int dtype, int k, int cta);
-const void* cpasync_kernel(int dtype, int d);
+const void* cpasync_kernel(int dtype, int d, int g);  // g: copies per commit group
 const void* ldsts_kernel(int dtype, int g);
 const void* tma_kernel(int dtype);
 const void* tma_warp_kernel(int dtype);
@@ -69,7 +69,7 @@ const void* ldg_fixed_kernel(int dtype, int k, int cta);
 const void* ldg_cov_kernel(int k, int cta, bool dyn);
 const void* ldg32_cov_kernel(int k, int cta, bool dyn);
 const void* ldg_fixed_cov_kernel(int k, int cta);
-const void* cpasync_cov_kernel(int d);
+const void* cpasync_cov_kernel(int d, int g);
 const void* ldsts_cov_kernel(int g);
 const void* tma_cov_kernel();
 const void* tma_warp_cov_kernel();

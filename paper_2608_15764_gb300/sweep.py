@@ -25,6 +25,9 @@ GPU and checked against the first cell's checksum):
        kernel at equal offered groups G in {1,2,4,8,12,16} (cp.async depth D =
        G; G loads staged through shared memory), at 1 and 8 warps per SM (one
        CTA per SM), on 1 GiB.
+  cpgroups  cp.async with G in {1,2,4,8} 16-byte copies per commit group
+       and D groups in flight (D*G <= 16): every cell at 256 threads on
+       4 GiB, and one warp (32 threads, one CTA) on 32 MiB.
   ladder  paper §4.1: pointer-chase latency versus footprint, .ca / .cg.
   l2   the L2-targeted backend (paper §4.2 "L2-targeted control"): 16, 32
        and 64 MiB buffers (below the 129 MB L2) read 4 GiB / size passes per
@@ -184,6 +187,17 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
             yield dict(mech="ldg", k=k, cta=32, grid=1, gib=1 / 32)
         for d in (1, 2, 4, 8):
             yield dict(mech="cpasync", k=d, cta=32, grid=1, gib=1 / 32)
+    elif config == "cpgroups":
+        # cp.async with G copies per commit group and D groups in flight: the
+        # whole grid at 4 GiB (D*G*16 bytes in flight per thread), and a lone
+        # warp, whose time shows the offered concurrency directly
+        for g in (1, 2, 4, 8):
+            for d in range(1, 16 // g + 1):
+                yield dict(mech="cpasync", k=d, copies=g, cta=256, grid=0, gib=4)
+        for g in (1, 2, 4, 8):
+            for d in (1, 2, 4, 8, 16):
+                if d * g <= 16:
+                    yield dict(mech="cpasync", k=d, copies=g, cta=32, grid=1, gib=1 / 32)
     elif config == "primary":
         for k in (1, 2, 4, 8):
             yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=4)
@@ -215,7 +229,10 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
             yield dict(mech="tma", stage_bytes=p.stage_bytes, stages=p.stages, cta=p.cta, grid=0, gib=gib,
                        ring="warp" if p.ring else "cta")
         else:
-            yield dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop, trav=p.order, gib=gib)
+            cell = dict(mech=MECH_NAMES[p.mech], k=p.k, cta=p.cta, grid=0, cop=p.cop, trav=p.order, gib=gib)
+            if p.copies != 1:
+                cell["copies"] = p.copies
+            yield cell
     elif config == "ncu-cpskew":
         for skew in (0, 1):
             yield dict(mech="cpasync", k=4, cta=256, grid=0, skew=skew, gib=1)
@@ -287,7 +304,8 @@ def run(config: str, out: str | None, repeats: int = 10, orders=("asc", "desc"),
                     cfg = sl.config("tma", stage_bytes=c["stage_bytes"], stages=c["stages"], ring=c.get("ring", "cta"),
                                     **kw)
                 else:
-                    cfg = sl.config(c["mech"], k=c["k"], cop=c.get("cop", 0), order=c.get("trav", 0), **kw)
+                    cfg = sl.config(c["mech"], k=c["k"], cop=c.get("cop", 0), order=c.get("trav", 0),
+                                    copies=c.get("copies", 1), **kw)
                 status, resident = 0, 0
                 try:
                     plan = sl.sl_plan(nbytes, dt, cfg)
@@ -665,7 +683,7 @@ def main(argv=None):
                     help="write --traffic-out from single-launch ncu-point captures instead of running a sweep")
     ap.add_argument("--traffic-out", default=os.path.join("profiles", "traffic.json"))
     ap.add_argument("--config", required=False,
-                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "c3", "c4", "ilp", "primary",
+                    choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "cpgroups", "c3", "c4", "ilp", "primary",
                              "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "l2", "cpratio", "ladder", "k1gate", "two",
                              "launches"])
     ap.add_argument("--out", default=None)

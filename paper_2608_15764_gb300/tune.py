@@ -29,6 +29,7 @@ class Point:
     stage_bytes: int = 0  # TMA
     stages: int = 0       # TMA
     ring: int = SL_RING_CTA  # TMA: one ring per CTA or per warp
+    copies: int = 1       # cp.async: 16-byte copies per commit group (G)
     cop: int = 0
     order: int = 0        # SL_ASC, or SL_DYN (dynamic contiguous chunks, LDG)
     gbs: list = field(default_factory=list)  # per repeat
@@ -46,6 +47,8 @@ class Point:
                         ring=self.ring)
         else:
             base = dict(k=self.k, cta=self.cta, grid=self.grid, cop=self.cop)
+            if self.copies != 1:
+                base["copies"] = self.copies
             if self.order:
                 base["order"] = self.order
         base.update(kw)
@@ -75,15 +78,17 @@ class Point:
         """Offered in-flight bytes per CTA (for tie-breaking)."""
         if self.mech == SL_TMA:
             return self.stage_bytes * self.stages
-        return self.k * self.cta * (32 if self.mech == SL_LDG32 else 16)
+        return self.k * self.copies * self.cta * (32 if self.mech == SL_LDG32 else 16)
 
     def label(self) -> str:
         if self.mech == SL_TMA:
             ring = " per-warp stages" if self.ring == SL_RING_WARP else ""
             return f"tma S={self.stage_bytes // 1024}K x{self.stages} cta={self.cta}{ring}"
         dyn = " dyn" if self.order == 2 else ""
-        kd = "D" if self.mech == SL_CPASYNC else "K"
-        return f"{MECH_NAMES[self.mech]} {kd}={self.k} cta={self.cta} cop={self.cop}{dyn}"
+        if self.mech == SL_CPASYNC:
+            g = f" G={self.copies}" if self.copies != 1 else ""
+            return f"cpasync D={self.k}{g} cta={self.cta}"
+        return f"{MECH_NAMES[self.mech]} K={self.k} cta={self.cta} cop={self.cop}{dyn}"
 
     def spec(self) -> str:
         """The point in parse_point's notation."""
@@ -92,6 +97,8 @@ class Point:
         name = MECH_NAMES[self.mech] + ("dyn" if self.order == 2 else "")
         if self.mech == SL_LDG and self.order != 2:
             return f"ldg:{self.k}:{self.cta}:{self.cop}"
+        if self.mech == SL_CPASYNC and self.copies != 1:
+            return f"cpasync:{self.k}:{self.cta}:{self.copies}"
         return f"{name}:{self.k}:{self.cta}"
 
     def as_dict(self) -> dict:
@@ -105,11 +112,13 @@ class Point:
                      ring="warp" if self.ring == SL_RING_WARP else "cta")
         else:
             d.update(k=self.k, cop=self.cop, order=self.order)
+            if self.mech == SL_CPASYNC:
+                d.update(copies=self.copies)
         return d
 
 
 def parse_point(text: str) -> Point:
-    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta',
+    """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta[:G]',
     'tma:stage_bytes:stages:cta' (one ring per CTA, producer warp) or 'tmaw:stage_bytes:stages[:cta]'
     (the CTA's stages dealt to its warps; cta defaults to warp_ring_cta)."""
     f = text.split(":")
@@ -123,9 +132,11 @@ def parse_point(text: str) -> Point:
     mech = f[0]
     if mech == "tma":
         return Point(SL_TMA, stage_bytes=int(f[1]), stages=int(f[2]), cta=int(f[3]) if len(f) > 3 else 256)
-    if mech in ("ldg", "cpasync"):
-        return Point(SL_LDG if mech == "ldg" else SL_CPASYNC, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256,
-                     cop=int(f[3]) if len(f) > 3 else 0)
+    if mech == "ldg":
+        return Point(SL_LDG, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256, cop=int(f[3]) if len(f) > 3 else 0)
+    if mech == "cpasync":
+        return Point(SL_CPASYNC, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256,
+                     copies=int(f[3]) if len(f) > 3 else 1)
     raise ValueError(f"bad point {text!r}")
 
 
@@ -135,13 +146,17 @@ def warp_ring_cta(stage_bytes: int, stages: int) -> int:
     return 32 * stages
 
 
+# cp.async points with several copies per commit group (D, G): the same bytes
+# in flight as D*G one-copy groups, with fewer commits and waits
+CP_GROUP_POINTS = ((1, 2), (2, 2), (1, 4), (2, 4), (1, 8))
 TMA_STAGE_BYTES = (4096, 16384, 65536)
 TMA_STAGES = tuple(range(2, 9))
 
 
 def default_points(cta: int = 256) -> list[Point]:
     """The K-response catalogue: LDG K 1-16 (16 bytes, .cg), four .L2::256B
-    points, the dynamic-chunk traversal, 32-byte loads, cp.async D 1-8, and
+    points, the dynamic-chunk traversal, 32-byte loads, cp.async D 1-8 (and
+    five points with 2-8 copies per commit group), and
     TMA stage sizes 4/16/64 KiB x 2-8 stages in both ring layouts (read by
     all `cta` consumer threads, and by 128 for 4 KiB stages; dealt to the
     warps, one stage per warp and, for even stage counts, two).
@@ -154,6 +169,7 @@ def default_points(cta: int = 256) -> list[Point]:
     pts += [Point(SL_LDG32, k=k, cta=cta) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_LDG32, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in range(1, 9)]
+    pts += [Point(SL_CPASYNC, k=d, cta=cta, copies=g) for d, g in CP_GROUP_POINTS]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n) for s in TMA_STAGE_BYTES for n in TMA_STAGES]
     # with 4 KiB stages a 256-thread CTA gives each consumer lane a single
     # 16-byte vector per stage; 128 consumer threads read two

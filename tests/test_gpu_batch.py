@@ -133,6 +133,7 @@ def test_batch_errors(sl):
         # the batched TMA class kernel runs one ring per CTA
         ([(d, 1024, wl.U32)], autotune.plain_table(sl.config("tma", cta=256, stage_bytes=4096, stages=8, ring="warp")),
          sl.SL_ERR_ARG),
+        ([(d, 1024, wl.U32)], autotune.plain_table(sl.config("cpasync", k=2, copies=4, cta=256)), sl.SL_ERR_ARG),
     ]
     for bufs, table, code in cases:
         with pytest.raises(E) as e:

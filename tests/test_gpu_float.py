@@ -95,9 +95,9 @@ def test_ldsts_float(sl, payloads, dt, g):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("d", [1, 2, 4, 8])
-def test_cpasync_float(sl, payloads, dt, d):
-    _check(sl, payloads[dt], dt, sl.config("cpasync", k=d, cta=256))
+@pytest.mark.parametrize("d,g", [(1, 1), (2, 1), (4, 1), (8, 1), (1, 2), (3, 2), (8, 2), (2, 4), (4, 4), (1, 8), (2, 8)])
+def test_cpasync_float(sl, payloads, dt, d, g):
+    _check(sl, payloads[dt], dt, sl.config("cpasync", k=d, copies=g, cta=256))
 
 
 @pytest.mark.parametrize("dt", DTYPES)

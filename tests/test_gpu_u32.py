@@ -88,6 +88,20 @@ def test_ldsts_and_deep_cpasync(sl, data, g, cta):
     _check(sl, dev, NBYTES, want, sl.config("cpasync", k=g, cta=cta, order="desc"))
 
 
+CP_GROUPS = [(d, g) for g in (2, 4, 8) for d in range(1, 16 // g + 1)]
+
+
+@pytest.mark.parametrize("d,g", CP_GROUPS)
+@pytest.mark.parametrize("cta", [32, 256, 512])
+@pytest.mark.parametrize("order", ["asc", "desc"])
+def test_cpasync_copies_per_group(sl, data, d, g, cta, order):
+    """cp.async with G copies per commit group and D groups in flight: the
+    ring holds D*G slots per thread and a tile is cta*D*G vectors."""
+    dev, _, want = data
+    r = _check(sl, dev, NBYTES, want, sl.config("cpasync", k=d, copies=g, cta=cta, order=order))
+    assert r.smem_bytes == d * g * cta * 16
+
+
 @pytest.mark.parametrize("stage", [4096, 16384, 65536])
 @pytest.mark.parametrize("stages", [2, 3, 4, 8])
 @pytest.mark.parametrize("order", ["asc", "desc"])
@@ -144,6 +158,7 @@ def test_tma_warp_ring_needs_warps_dividing_stages(sl, data):
 
 
 @pytest.mark.parametrize("mech,kw", [("ldg", {"k": 2}), ("ldg", {"k": 13}), ("cpasync", {"k": 3}),
+                                     ("cpasync", {"k": 3, "copies": 2}), ("cpasync", {"k": 2, "copies": 8}),
                                      ("tma", {"stage_bytes": 4096, "stages": 3}),
                                      ("tma", {"stage_bytes": 4096, "stages": 8, "ring": "warp"})])
 @pytest.mark.parametrize("passes", [2, 3])
@@ -155,6 +170,7 @@ def test_passes_closed_form(sl, data, mech, kw, passes):
 
 @pytest.mark.parametrize("nvec", [0, 1, 2, 3, 31, 33, 255, 257, 4096 + 5])
 @pytest.mark.parametrize("mech,kw", [("ldg", {"k": 1}), ("ldg", {"k": 16}), ("cpasync", {"k": 8}),
+                                     ("cpasync", {"k": 1, "copies": 8}), ("cpasync", {"k": 5, "copies": 2}),
                                      ("tma", {"stage_bytes": 4096, "stages": 2}),
                                      ("tma", {"stage_bytes": 4096, "stages": 8, "ring": "warp"}),
                                      ("tma", {"stage_bytes": 65536, "stages": 2, "ring": "warp", "cta": 32})])
@@ -199,6 +215,15 @@ def test_smem_skew_keeps_results(sl, data, mech, k, skew):
                   cfg=sl.config(mech, k=k, cta=256, debug_flags=sl.SL_DEBUG_SMEM_SKEW(skew)))
     assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, NBYTES // 16)
     assert r.smem_bytes == k * 256 * 16 + 128
+
+
+@pytest.mark.parametrize("skew", [1, 7])
+def test_smem_skew_with_copies_per_group(sl, data, skew):
+    dev, _, want = data
+    r = sl.sl_run(dev, nbytes=NBYTES, dtype=sl.SL_U32,
+                  cfg=sl.config("cpasync", k=2, copies=4, cta=256, debug_flags=sl.SL_DEBUG_SMEM_SKEW(skew)))
+    assert (r.sum_u32, r.xor_u64, r.issued_loads) == (*want, NBYTES // 16)
+    assert r.smem_bytes == 2 * 4 * 256 * 16 + 128
 
 
 def test_ldg4_rejects_other_forms(sl, data):
@@ -298,7 +323,8 @@ def test_offset_views(sl, data):
     dev, host, _ = data
     nbytes = NBYTES - 64
     want = oracle.checksum(host[4: 4 + nbytes // 4])
-    for cfg in [sl.config("ldg", k=4), sl.config("cpasync", k=2), sl.config("tma", stage_bytes=16384, stages=4)]:
+    for cfg in [sl.config("ldg", k=4), sl.config("cpasync", k=2), sl.config("cpasync", k=3, copies=4),
+                sl.config("tma", stage_bytes=16384, stages=4)]:
         r = sl.sl_run(dev.data_ptr() + 16, nbytes=nbytes, dtype=sl.SL_U32, cfg=cfg)
         assert (r.sum_u32, r.xor_u64) == want
 
@@ -315,6 +341,14 @@ def test_argument_errors(sl, data):
         (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", cta=64)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=17)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("ldsts", k=0)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=2, copies=3)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=2, copies=16)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=2, copies=-1)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=3, copies=8)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=9, copies=2)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldg", k=2, copies=2)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("ldsts", k=2, copies=2)), sl.SL_ERR_ARG),
+        (dict(buf=dev, nbytes=1024, cfg=sl.config("cpasync", k=4, copies=4, cta=1024)), sl.SL_ERR_INFEASIBLE),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stage_bytes=8192)), sl.SL_ERR_INFEASIBLE),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stages=1)), sl.SL_ERR_ARG),
         (dict(buf=dev, nbytes=1024, cfg=sl.config("tma", stage_bytes=65536, stages=4)), sl.SL_ERR_INFEASIBLE),

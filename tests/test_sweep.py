@@ -114,13 +114,18 @@ def test_tune_points_specs_loads_and_choice():
     pts = tune.default_points()
     for p in pts:
         q = tune.parse_point(p.spec())
-        assert (q.mech, q.k, q.cta, q.order, q.stage_bytes, q.stages, q.ring) == \
-            (p.mech, p.k, p.cta, p.order, p.stage_bytes, p.stages, p.ring), p.spec()
+        assert (q.mech, q.k, q.cta, q.order, q.stage_bytes, q.stages, q.ring, q.copies) == \
+            (p.mech, p.k, p.cta, p.order, p.stage_bytes, p.stages, p.ring, p.copies), p.spec()
     # the catalogue: LDG K 1-16, cp.async D 1-8, TMA 4/16/64 KiB x 2-8 in both ring layouts, every
     # per-warp point with a warp count dividing its stage count
     from paper_2608_15764_gb300 import SL_CPASYNC, SL_LDG, SL_RING_WARP, SL_TMA
     assert sorted(q.k for q in pts if q.mech == SL_LDG and q.order == 0 and q.cop == 0) == list(range(1, 17))
-    assert sorted(q.k for q in pts if q.mech == SL_CPASYNC) == list(range(1, 9))
+    assert sorted(q.k for q in pts if q.mech == SL_CPASYNC and q.copies == 1) == list(range(1, 9))
+    assert {(q.k, q.copies) for q in pts if q.mech == SL_CPASYNC and q.copies > 1} == {(1, 2), (2, 2), (1, 4),
+                                                                                       (2, 4), (1, 8)}
+    g = tune.parse_point("cpasync:2:256:4")
+    assert (g.k, g.copies, g.offered, g.spec()) == (2, 4, 2 * 4 * 256 * 16, "cpasync:2:256:4")
+    assert g.cfg().copies == 4 and g.label() == "cpasync D=2 G=4 cta=256" and g.as_dict()["copies"] == 4
     for ring in (0, SL_RING_WARP):
         got = {(q.stage_bytes, q.stages) for q in pts if q.mech == SL_TMA and q.ring == ring}
         assert got == {(s, n) for s in (4096, 16384, 65536) for n in range(2, 9)}
