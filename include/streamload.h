@@ -347,8 +347,8 @@ int sl_chase(const void* dev_chain, uint64_t bytes, uint32_t start, uint64_t war
  * vectors q+1).  Instantiations exist for: SL_LDG K 1/3/8/16 grid-stride and
  * K 2/12 SL_DYN at cta 128/256/512 (SL_COP_CG); SL_LDG32 K 1/3/8 at cta 256
  * (grid-stride or SL_DYN); the fixed-iteration control at K 2/8, cta 256/1024;
- * SL_CPASYNC D 1/4/16; SL_LDSTS G 1/16; SL_TMA (either ring layout) -- SL_ERR_ARG
- * otherwise.  A debug tool (the counting atomics slow the kernel); no paper
+ * SL_CPASYNC D 1/4/16 (one copy per group) and D x G = 2 x 4, 3 x 2; SL_LDSTS
+ * G 1/16; SL_TMA (either ring layout) -- SL_ERR_ARG otherwise.  A debug tool (the counting atomics slow the kernel); no paper
  * counterpart. */
 int sl_coverage(const void* dev_buf, uint64_t bytes, const sl_config* cfg, uint32_t* dev_counts, sl_result* out);
 
@@ -401,7 +401,8 @@ typedef struct sl_batch_desc {
  * cfg: mech, k (LDG K in {1,2,3,4,6,8,12,16}, cp.async D 1..8), stage_bytes,
  * stages, cta (LDG: 128/256/512) and grid (<= 0: resident CTAs per SM x
  * SMs, a persistent grid) are used (TMA classes run one ring per CTA:
- * tma_ring must be SL_RING_CTA); order, passes, flush_l2, cop, debug_flags
+ * tma_ring must be SL_RING_CTA; cp.async classes put one copy in each commit
+ * group: copies must be 0 or 1); order, passes, flush_l2, cop, debug_flags
  * and stream are ignored. */
 typedef struct sl_tune_entry {
     uint64_t  min_bytes;
