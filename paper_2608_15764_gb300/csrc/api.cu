@@ -217,6 +217,12 @@ int occupancy(DevCtx* c, const void* fn, int block, size_t smem, int* out) {
 // G, the 16-byte copies per commit group of SL_CPASYNC (0 in the config means 1).
 int copies_per_group(const sl_config* cfg) { return cfg->copies == 0 ? 1 : cfg->copies; }
 
+// SL_RING_CTA: vectors a consumer thread reads into registers before folding
+// them.  4 where each of the cta consumer threads reads at least 4 vectors of
+// a stage; 1 below that, where the registers of a larger batch would cost
+// CTAs per SM (measured: 4 KiB stages read by 128 or 256 threads).
+int tma_batch(const sl_config* cfg) { return cfg->stage_bytes / 16 >= 4 * cfg->cta ? 4 : 1; }
+
 int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const sl_config* cfg, Plan* p) {
     if (!cfg) return fail(SL_ERR_ARG, "cfg is NULL");
     if (dtype < SL_U32 || dtype > SL_FP8_E4M3) return fail(SL_ERR_ARG, "bad dtype %d", dtype);
@@ -329,12 +335,12 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
             if (cfg->stages % (cta / 32) != 0)
                 return fail(SL_ERR_ARG, "SL_RING_WARP deals the %d stages to %d warps: the warp count must divide "
                             "the stage count", cfg->stages, cta / 32);
-            p->fn = sl::tma_warp_kernel(dtype);
+            p->fn = sl::tma_warp_kernel(dtype, dtype == SL_BF16 && cfg->stages == cta / 32);
             p->block = cta;
             p->smem = static_cast<size_t>(cfg->stages) * (static_cast<size_t>(cfg->stage_bytes) + 8);
         } else if (cfg->tma_ring == SL_RING_CTA) {
             if (cta > 992) return fail(SL_ERR_ARG, "TMA consumer threads %d > 992", cta);
-            p->fn = sl::tma_kernel(dtype);
+            p->fn = sl::tma_kernel(dtype, tma_batch(cfg));
             p->block = cta + 32;
             p->smem = static_cast<size_t>(cfg->stages) * cfg->stage_bytes;
         } else {
@@ -389,10 +395,13 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     const uint64_t fixed_iters = fixed ? cfg->target_loads / (static_cast<uint64_t>(grid) * tile_vec) : 0;
     const uint64_t ntiles = fixed ? fixed_iters * static_cast<uint64_t>(grid) : (units + tile_vec - 1) / tile_vec;
     p->grid = (nvec == 0 || (fixed && fixed_iters == 0)) ? 0 : grid;
-    // The kernels count tiles and per-thread loads in 32 bits.
+    // The kernels count tiles and per-thread loads in 32 bits (the per-warp
+    // TMA ring's chunk index runs up to total + stages * grid).
     const uint64_t total = ntiles * passes;
     const uint64_t per_thread = ((total + grid - 1) / grid) * ((tile_vec + cta - 1) / cta);
-    if (total + static_cast<uint64_t>(grid) >= (1ull << 32) || per_thread >= (1ull << 32))
+    const uint64_t ahead = static_cast<uint64_t>(grid) *
+                           ((cfg->mech == SL_TMA && cfg->tma_ring == SL_RING_WARP) ? cfg->stages : 1);
+    if (total + ahead >= (1ull << 32) || per_thread >= (1ull << 32))
         return fail(SL_ERR_ARG, "passes x tiles too large for one launch (%llu tiles); lower passes",
                     (unsigned long long)total);
     KArgs& a = p->args;
@@ -451,7 +460,7 @@ const void* coverage_fn(const sl_config* cfg) {
     case SL_LDG32: return sl::ldg32_cov_kernel(cfg->k, cfg->cta, dyn);
     case SL_CPASYNC: return sl::cpasync_cov_kernel(cfg->k, copies_per_group(cfg));
     case SL_LDSTS: return sl::ldsts_cov_kernel(cfg->k);
-    case SL_TMA: return cfg->tma_ring == SL_RING_WARP ? sl::tma_warp_cov_kernel() : sl::tma_cov_kernel();
+    case SL_TMA: return cfg->tma_ring == SL_RING_WARP ? sl::tma_warp_cov_kernel() : sl::tma_cov_kernel(tma_batch(cfg));
     default: return nullptr;
     }
 }

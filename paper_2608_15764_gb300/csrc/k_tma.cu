@@ -31,7 +31,7 @@
 
 namespace sl {
 
-template <int DT, bool COV = false>
+template <int DT, int B, bool COV = false>
 __global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ __align__(8) uint64_t full[SL_MAX_STAGES];
@@ -109,13 +109,32 @@ __global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
             const uint64_t left = bytes - off;
             const uint32_t nv = (left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes) >> 4;
             const uint32_t base = ring0 + s * stage_bytes;
-#pragma unroll 4
-            for (uint32_t v = ct; v < nv; v += nct) {
-                acc.fold(lds16(base + 16u * v));
-                acc.n += 1;
+            // A thread's vectors of the stage are ct, ct + nct, ...: batches of
+            // B while more than B remain, then the last batch (up to B) is
+            // read into registers and the warp releases the stage before
+            // folding it, so the producer's refill overlaps that fold.
+            uint32_t v = ct;
+#pragma unroll 1
+            for (; v + B * nct < nv; v += B * nct) {
+                uint4 x[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) x[u] = lds16(base + 16u * (v + u * nct));
+#pragma unroll
+                for (int u = 0; u < B; ++u) acc.fold(x[u]);
+                acc.n += B;
             }
+            uint4 x[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (v + u * nct < nv) x[u] = lds16(base + 16u * (v + u * nct));
             __syncwarp();
             if (lane == 0) mbar_arrive(empty0 + 8 * s);
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (v + u * nct < nv) {
+                    acc.fold(x[u]);
+                    acc.n += 1;
+                }
             if (++s == nst) { s = 0; ++r; }
         }
     }
@@ -147,7 +166,7 @@ __global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
 //
 // The warp count divides the stage count (at most SL_MAX_STAGES), so a CTA has
 // at most SL_MAX_STAGES warps; registers are capped for four such CTAs per SM.
-template <int DT, bool COV = false>
+template <int DT, bool EARLY, bool COV = false>
 __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs a) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ volatile int abort_flag;
@@ -156,15 +175,16 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
     cta_start(a);
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const uint32_t nst = static_cast<uint32_t>(a.nst) / nw;  // stages of this warp (the host checks W | stages)
-    const uint64_t nchunks = a.ntiles;
-    const uint64_t total = a.total;
+    // chunk indices fit in 32 bits: the host checks total + grid * W < 2^32
+    const uint32_t nchunks = static_cast<uint32_t>(a.ntiles);
+    const uint32_t total = static_cast<uint32_t>(a.total);
     const uint32_t stage_bytes = a.tile_vec * 16u;
     const uint64_t bytes = a.nvec * 16ull;
     const uint8_t* __restrict__ gbuf = static_cast<const uint8_t*>(a.buf);
     const uint32_t my_ring = smem_addr(ring) + warp * nst * stage_bytes;
     const uint32_t my_full = smem_addr(ring) + static_cast<uint32_t>(a.nst) * stage_bytes + warp * nst * 8u;
-    const uint64_t G = static_cast<uint64_t>(gridDim.x) * nw;
-    const uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * nw + warp;
+    const uint32_t G = gridDim.x * nw;
+    const uint32_t g0 = blockIdx.x * nw + warp;
     // debug: global warp 0 leaves its first chunk unarmed (it has one whenever
     // the buffer is not empty), so its first wait runs out
     const bool skip_one = (a.debug & SL_DEBUG_TMA_SKIP_STAGE) && g0 == 0;
@@ -181,16 +201,16 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
     __syncthreads();
 
     // byte offset and length of chunk c
-    const auto piece = [&](uint64_t c, uint64_t& off, uint32_t& len) {
-        uint64_t t = c < nchunks ? c : c % nchunks;
+    const auto piece = [&](uint32_t c, uint64_t& off, uint32_t& len) {
+        uint32_t t = c < nchunks ? c : c % nchunks;
         if (a.desc) t = nchunks - 1 - t;
-        off = t * stage_bytes;
+        off = static_cast<uint64_t>(t) * stage_bytes;
         const uint64_t left = bytes - off;
         len = left < stage_bytes ? static_cast<uint32_t>(left) : stage_bytes;
     };
     uint32_t armed = 0;     // lane 0: bit s = stage s has had a copy issued
     uint32_t last_par = 0;  // lane 0: bit s = parity of the phase of stage s's last copy
-    const auto issue = [&](uint32_t s, uint32_t par, uint64_t c, uint32_t j) {
+    const auto issue = [&](uint32_t s, uint32_t par, uint32_t c, uint32_t j) {
         if (skip_one && j == 0) return;  // the warp's j-th chunk (debug only)
         uint64_t off;
         uint32_t len;
@@ -205,7 +225,7 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
     };
     if (lane == 0) {
         for (uint32_t j = 0; j < nst; ++j) {
-            const uint64_t c = g0 + j * G;
+            const uint32_t c = g0 + j * G;
             if (c >= total) break;
             issue(j, 0u, c, j);
         }
@@ -214,13 +234,30 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
     Acc<DT> acc;
     uint32_t s = 0, r = 0;  // stage and round of the warp's current chunk (its j-th: j = r*nst + s)
 #pragma unroll 1
-    for (uint64_t c = g0; c < total; c += G) {
+    for (uint32_t c = g0; c < total; c += G) {
         const bool got = bounded_wait(my_full + 8 * s, r & 1u, &cta_err, a.timeout_ns, &abort_flag, true,
                                       DEV_ERR_TIMEOUT_FULL);
         if (!__all_sync(FULL_MASK, got)) break;  // warp-uniform exit
         uint64_t off;
         uint32_t len;
         piece(c, off, len);
+        // Once every lane has read stage s (__syncwarp), lane 0 refills it.
+        // EARLY: a full stage is refilled as soon as its last batch of
+        // vectors is in registers, before that batch is folded, so the
+        // refill's memory latency overlaps the fold.  Otherwise the stage is
+        // refilled after the fold.  The host takes EARLY for BF16 payloads
+        // (the longest fold) where each warp owns a single stage: 5-14%
+        // faster there, while with two stages per warp (the other one in
+        // flight during the fold) and for the shorter folds it measured
+        // no faster or slower.
+        const auto refill = [&]() {
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const uint32_t cn = c + nst * G;
+                if (cn < total) issue(s, (r + 1) & 1u, cn, (r + 1) * nst + s);
+            }
+        };
         const uint32_t base = my_ring + s * stage_bytes + 16u * lane;
         if (len == stage_bytes) {
             const uint32_t per_lane = stage_bytes >> 9;  // a multiple of 8
@@ -229,10 +266,12 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
                 uint4 v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[u] = lds16(base + 512u * (i + u));
+                if (EARLY && i + 8 == per_lane) refill();
 #pragma unroll
                 for (int u = 0; u < 8; ++u) acc.fold(v[u]);
             }
             acc.n += per_lane;
+            if (!EARLY) refill();
         } else {
             const uint32_t nv = len >> 4;
 #pragma unroll 1
@@ -240,12 +279,7 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
                 acc.fold(lds16(my_ring + s * stage_bytes + 16u * v));
                 acc.n += 1;
             }
-        }
-        __syncwarp();  // every lane has read stage s
-        if (lane == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const uint64_t cn = c + nst * G;
-            if (cn < total) issue(s, (r + 1) & 1u, cn, (r + 1) * nst + s);
+            refill();
         }
         if (++s == nst) { s = 0; ++r; }
     }
@@ -261,27 +295,38 @@ __global__ void __launch_bounds__(SL_MAX_STAGES * 32, 4) k_tma_warp(const KArgs 
     cta_finish<DT>(acc, true, warp, nw, a, &cta_err);
 }
 
-const void* tma_cov_kernel() { return reinterpret_cast<const void*>(&k_tma<SL_U32, true>); }
-const void* tma_warp_cov_kernel() { return reinterpret_cast<const void*>(&k_tma_warp<SL_U32, true>); }
+const void* tma_cov_kernel(int batch) {
+    return batch == 4 ? reinterpret_cast<const void*>(&k_tma<SL_U32, 4, true>)
+                      : reinterpret_cast<const void*>(&k_tma<SL_U32, 1, true>);
+}
+const void* tma_warp_cov_kernel() { return reinterpret_cast<const void*>(&k_tma_warp<SL_U32, false, true>); }
 
-const void* tma_warp_kernel(int dtype) {
+const void* tma_warp_kernel(int dtype, bool early) {
+    if (early) return dtype == SL_BF16 ? reinterpret_cast<const void*>(&k_tma_warp<SL_BF16, true>) : nullptr;
     switch (dtype) {
-    case SL_U32: return reinterpret_cast<const void*>(&k_tma_warp<SL_U32>);
-    case SL_F32: return reinterpret_cast<const void*>(&k_tma_warp<SL_F32>);
-    case SL_BF16: return reinterpret_cast<const void*>(&k_tma_warp<SL_BF16>);
-    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&k_tma_warp<SL_FP8_E4M3>);
+    case SL_U32: return reinterpret_cast<const void*>(&k_tma_warp<SL_U32, false>);
+    case SL_F32: return reinterpret_cast<const void*>(&k_tma_warp<SL_F32, false>);
+    case SL_BF16: return reinterpret_cast<const void*>(&k_tma_warp<SL_BF16, false>);
+    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&k_tma_warp<SL_FP8_E4M3, false>);
     default: return nullptr;
     }
 }
 
-const void* tma_kernel(int dtype) {
+template <int B>
+static const void* tma_for(int dtype) {
     switch (dtype) {
-    case SL_U32: return reinterpret_cast<const void*>(&k_tma<SL_U32>);
-    case SL_F32: return reinterpret_cast<const void*>(&k_tma<SL_F32>);
-    case SL_BF16: return reinterpret_cast<const void*>(&k_tma<SL_BF16>);
-    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&k_tma<SL_FP8_E4M3>);
+    case SL_U32: return reinterpret_cast<const void*>(&k_tma<SL_U32, B>);
+    case SL_F32: return reinterpret_cast<const void*>(&k_tma<SL_F32, B>);
+    case SL_BF16: return reinterpret_cast<const void*>(&k_tma<SL_BF16, B>);
+    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&k_tma<SL_FP8_E4M3, B>);
     default: return nullptr;
     }
+}
+
+const void* tma_kernel(int dtype, int batch) {
+    if (batch == 4) return tma_for<4>(dtype);
+    if (batch == 1) return tma_for<1>(dtype);
+    return nullptr;
 }
 
 }  // namespace sl

@@ -57,8 +57,13 @@ const void* ldg_kernel(int dtype, int k, int cta, int cop);
 const void* ldg_dyn_kernel(int dtype, int k, int cta);
 const void* cpasync_kernel(int dtype, int d, int g);  // g: copies per commit group
 const void* ldsts_kernel(int dtype, int g);
-const void* tma_kernel(int dtype);
-const void* tma_warp_kernel(int dtype);
+// SL_RING_CTA: batch = vectors a consumer thread reads into registers at a
+// time (4, or 1 where a thread reads fewer than 4 vectors of a stage)
+const void* tma_kernel(int dtype, int batch);
+// SL_RING_WARP: early = refill a stage before folding its last batch
+// (instantiated for BF16 payloads; the host takes it where each warp owns a
+// single stage)
+const void* tma_warp_kernel(int dtype, bool early);
 const void* ldg4_kernel(int dtype, int k, int cta);
 const void* ldg32_kernel(int dtype, int k, int cta, bool dyn);
 const void* ldg_fixed_kernel(int dtype, int k, int cta);
@@ -71,7 +76,7 @@ const void* ldg32_cov_kernel(int k, int cta, bool dyn);
 const void* ldg_fixed_cov_kernel(int k, int cta);
 const void* cpasync_cov_kernel(int d, int g);
 const void* ldsts_cov_kernel(int g);
-const void* tma_cov_kernel();
+const void* tma_cov_kernel(int batch);
 const void* tma_warp_cov_kernel();
 
 // Two co-resident streams in one CTA (k_two.cu).  Stream A = warps
