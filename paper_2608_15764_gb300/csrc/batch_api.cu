@@ -19,7 +19,7 @@
 namespace sl {
 const void* batch_ldg_kernel(int dtype, int k, int cta);
 const void* batch_cpasync_kernel(int dtype, int d);
-const void* batch_tma_kernel(int dtype);
+const void* batch_tma_kernel(int dtype, int batch);
 cudaError_t launch_batch_combine(const BufSeg* segs, uint32_t nbuf, const WarpPartial* parts, const uint32_t* err,
                                  sl_result* out, cudaStream_t s);
 }  // namespace sl
@@ -134,7 +134,9 @@ int plan_group(Group& g, int sms, int smem_optin) {
         if (c.tma_ring != SL_RING_CTA)
             return bfail(SL_ERR_ARG, "tuning entry: the batched TMA class kernel has one ring per CTA "
                          "(tma_ring must be SL_RING_CTA)");
-        g.fn = sl::batch_tma_kernel(g.dtype);
+        // consumer threads read their last 4 vectors of a stage (1 where they
+        // read fewer) into registers before releasing it
+        g.fn = sl::batch_tma_kernel(g.dtype, c.stage_bytes / 16 >= 4 * c.cta ? 4 : 1);
         g.block = c.cta + 32;
         g.smem = static_cast<size_t>(c.stages) * c.stage_bytes;
         g.warps = c.cta / 32;

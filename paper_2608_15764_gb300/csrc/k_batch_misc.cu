@@ -70,8 +70,11 @@ constexpr uint32_t STAGE_LAST_OF_ITEM = 1, STAGE_DONE = 2;
 // item it belongs to.  Consumer warps fold every stage and write their item
 // partial after the item's last stage.  When the items run out the producer
 // arms one more stage marked DONE with a plain arrive (no bytes).  Waits are
-// bounded and issued copies are drained before exit, as in k_tma.
-template <int DT>
+// bounded and issued copies are drained before exit, as in k_tma.  As there,
+// a consumer thread reads its last B vectors of a stage into registers and
+// its warp releases the stage before folding them (B = 4, or 1 where a
+// thread reads fewer than 4 vectors of a stage).
+template <int DT, int B>
 __global__ void __launch_bounds__(1024) kb_tma(const BArgs a) {
     extern __shared__ __align__(128) uint8_t tma_ring[];
     __shared__ __align__(8) uint64_t full[SL_MAX_STAGES];
@@ -145,20 +148,35 @@ __global__ void __launch_bounds__(1024) kb_tma(const BArgs a) {
             const bool got =
                 bounded_wait(full0 + 8 * s, r & 1u, a.err, a.timeout_ns, &abort_flag, true, DEV_ERR_TIMEOUT_FULL);
             if (!__all_sync(FULL_MASK, got)) break;
-            const StageMeta m = meta[s];
+            const StageMeta m = meta[s];  // read before the stage is released
             if (m.flags & STAGE_DONE) break;
             const uint32_t base = ring0 + s * S;
-#pragma unroll 4
-            for (uint32_t v = ct; v < m.nv; v += nct) {
-                acc.fold(lds16(base + 16u * v));
-                acc.n += 1;
+            uint32_t v = ct;
+#pragma unroll 1
+            for (; v + B * nct < m.nv; v += B * nct) {
+                uint4 x[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) x[u] = lds16(base + 16u * (v + u * nct));
+#pragma unroll
+                for (int u = 0; u < B; ++u) acc.fold(x[u]);
+                acc.n += B;
             }
+            uint4 x[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (v + u * nct < m.nv) x[u] = lds16(base + 16u * (v + u * nct));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * s);
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (v + u * nct < m.nv) {
+                    acc.fold(x[u]);
+                    acc.n += 1;
+                }
             if (m.flags & STAGE_LAST_OF_ITEM) {
                 warp_item_store<DT>(acc, a.parts + m.part + (warp - 1));
                 acc = Acc<DT>();
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty0 + 8 * s);
             if (++s == nst) { s = 0; ++r; }
         }
     }
@@ -236,14 +254,21 @@ const void* batch_cpasync_kernel(int dtype, int d) {
     }
 }
 
-const void* batch_tma_kernel(int dtype) {
+template <int B>
+static const void* kb_tma_b(int dtype) {
     switch (dtype) {
-    case SL_U32: return reinterpret_cast<const void*>(&kb_tma<SL_U32>);
-    case SL_F32: return reinterpret_cast<const void*>(&kb_tma<SL_F32>);
-    case SL_BF16: return reinterpret_cast<const void*>(&kb_tma<SL_BF16>);
-    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&kb_tma<SL_FP8_E4M3>);
+    case SL_U32: return reinterpret_cast<const void*>(&kb_tma<SL_U32, B>);
+    case SL_F32: return reinterpret_cast<const void*>(&kb_tma<SL_F32, B>);
+    case SL_BF16: return reinterpret_cast<const void*>(&kb_tma<SL_BF16, B>);
+    case SL_FP8_E4M3: return reinterpret_cast<const void*>(&kb_tma<SL_FP8_E4M3, B>);
     default: return nullptr;
     }
+}
+
+const void* batch_tma_kernel(int dtype, int batch) {
+    if (batch == 4) return kb_tma_b<4>(dtype);
+    if (batch == 1) return kb_tma_b<1>(dtype);
+    return nullptr;
 }
 
 cudaError_t launch_batch_combine(const BufSeg* segs, uint32_t nbuf, const WarpPartial* parts, const uint32_t* err,
