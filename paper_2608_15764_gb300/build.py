@@ -31,15 +31,25 @@ HEADERS = ["sl_internal.h", "sl_device.cuh", "sl_mbar.cuh", "k_ldg.cuh", "k_batc
            os.path.join("..", "..", "include", "streamload.h")]
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and with whitespace runs collapsed
+    (the kernel sources hold no comment markers inside string literals)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the kernel sources (csrc/k_*, *.cuh, sl_internal.h): counters
-    taken on another version of the kernels are not reported against these."""
+    """Hash of the kernel code (csrc/k_*, *.cuh, sl_internal.h, comments and
+    layout left out): counters taken on another version of the kernels' code
+    are not reported against these."""
     import hashlib
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         if name.startswith("k_") or name.endswith(".cuh") or name == "sl_internal.h":
-            with open(os.path.join(CSRC, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+            with open(os.path.join(CSRC, name), encoding="utf-8") as f:
+                h.update(name.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -12,11 +12,13 @@
 //   full[s]  count 1: the producer arms it with arrive.expect_tx(bytes) and
 //            issues one cp.async.bulk global->shared that completes the
 //            transaction bytes;
-//   empty[s] count = consumer warps: each consumer warp arrives once it has
-//            read the stage.
+//   empty[s] count = consumer warps: each consumer warp arrives once all its
+//            lanes have read the stage into registers.
 // The producer waits on empty[s] before refilling stage s; consumers wait on
 // full[s], read the stage with ld.shared.v4 (thread t takes vectors t,
-// t+cta, ...) and fold.  No multicast is used anywhere.
+// t+cta, ...) and fold, B vectors at a time: the warp arrives on empty[s]
+// once its last batch is in registers and folds that batch afterwards, so
+// the refill overlaps the fold.  No multicast is used anywhere.
 //
 // Every wait is bounded: a wait that exceeds a.timeout_ns (by %globaltimer)
 // or a hard iteration cap records an error code in the CTA's shared error word
@@ -152,7 +154,10 @@ __global__ void __launch_bounds__(1024, 1) k_tma(const KArgs a) {
 // the warp has read stage s (__syncwarp), lane 0 re-arms it with
 // arrive.expect_tx and issues the warp's next cp.async.bulk into it, after a
 // proxy fence that orders the lanes' generic-proxy reads of the stage before
-// the bulk copy's async-proxy writes.
+// the bulk copy's async-proxy writes.  The lanes' reads precede the
+// __syncwarp in program order, which orders them before lane 0's fence and
+// copy whether or not their values have been used yet: the EARLY refill
+// below relies on that ordering alone.
 //
 // Chunks (stage-sized pieces of the buffer, the last one ragged) are dealt to
 // warps grid-wide: global warp g = blockIdx.x * W + w takes chunks g, g + G,

@@ -31,3 +31,15 @@ def test_tiles_per_mechanism():
     assert bench._tiles(sl.config("ldg", k=4, cta=256), 16 * 1025) == 2
     assert bench._tiles(sl.config("cpasync", k=2, cta=128), 16 * 256 * 3) == 3
     assert bench._tiles(sl.config("tma", stage_bytes=16384, stages=4), 16384 * 5 + 16) == 6
+
+
+def test_kernel_hash_ignores_comments_only():
+    """Counters stay attached to the kernels' code: comment and layout edits
+    keep the hash, any code edit changes it."""
+    from paper_2608_15764_gb300 import build
+    a = "int f(int x) {\n    return x + 1;  // one\n}\n"
+    b = "/* the same\n   function */\nint f(int x)\n{ return x + 1; }\n"
+    c = "int f(int x) {\n    return x + 2;  // one\n}\n"
+    assert build._code_only(a) == build._code_only(b)
+    assert build._code_only(a) != build._code_only(c)
+    assert len(build.kernel_source_hash()) == 16
