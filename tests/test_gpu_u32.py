@@ -150,6 +150,23 @@ def test_tma_warp_ring_shapes(sl, data, cta, grid, stages):
     assert r.grid == (grid or r.grid)
 
 
+def test_tma_warp_ring_chunk_count_limit(sl):
+    """The per-warp ring counts chunks in 32 bits up to total + stages x grid:
+    a launch whose chunk count is within that margin of 2^32 is refused for
+    SL_RING_WARP (SL_ERR_ARG) and planned for SL_RING_CTA.  Planning only."""
+    nbytes = 1 << 20                      # 256 chunks of 4 KiB
+    passes = ((1 << 32) - 1024) // 256    # total = 2^32 - 1024 chunks
+    warp = sl.config("tma", cta=256, stage_bytes=4096, stages=8, ring="warp", grid=608, passes=passes)
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_plan(nbytes, sl.SL_U32, warp)
+    assert e.value.status == sl.SL_ERR_ARG
+    ok = sl.sl_plan(nbytes, sl.SL_U32, sl.config("tma", cta=256, stage_bytes=4096, stages=8, grid=608, passes=passes))
+    assert ok.grid == 608
+    fewer = sl.sl_plan(nbytes, sl.SL_U32, sl.config("tma", cta=256, stage_bytes=4096, stages=8, ring="warp", grid=608,
+                                                    passes=passes - 32))
+    assert fewer.grid == 608
+
+
 def test_tma_warp_ring_needs_warps_dividing_stages(sl, data):
     dev, _, _ = data
     with pytest.raises(sl.SLError) as e:

@@ -44,7 +44,8 @@ def test_noalloc_matches_sl_run_two_calls(sl):
     exact = oracle.checksum(wl.splitmix_u32(1, NBYTES // 4))
     # two calls in a row with different launch shapes: the second must not
     # see anything of the first call's scratch contents
-    for cfg in [sl.config("ldg", k=4, cta=256), sl.config("ldg", k=2, cta=512, grid=37, order="desc")]:
+    for cfg in [sl.config("ldg", k=4, cta=256), sl.config("ldg", k=2, cta=512, grid=37, order="desc"),
+                sl.config("cpasync", k=2, copies=4, cta=256)]:
         want = sl.sl_run(dev, dtype=sl.SL_U32, cfg=cfg)
         got = _noalloc(sl, dev, sl.SL_U32, cfg)
         assert got.status == 0
