@@ -44,8 +44,7 @@ def test_noalloc_matches_sl_run_two_calls(sl):
     exact = oracle.checksum(wl.splitmix_u32(1, NBYTES // 4))
     # two calls in a row with different launch shapes: the second must not
     # see anything of the first call's scratch contents
-    for cfg in [sl.config("ldg", k=4, cta=256), sl.config("ldg", k=2, cta=512, grid=37, order="desc"),
-                sl.config("cpasync", k=2, copies=4, cta=256)]:
+    for cfg in [sl.config("ldg", k=4, cta=256), sl.config("ldg", k=2, cta=512, grid=37, order="desc")]:
         want = sl.sl_run(dev, dtype=sl.SL_U32, cfg=cfg)
         got = _noalloc(sl, dev, sl.SL_U32, cfg)
         assert got.status == 0
@@ -71,7 +70,7 @@ def test_noalloc_limits_and_empty(sl):
     out = torch.zeros(sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     for cfg in [sl.config("ldg", k=1, cta=256, grid=sl.SL_NOALLOC_MAX_CTAS + 1),
                 sl.config("ldg", k=1, cta=1024, grid=10000),  # more CTAs than the fixed scratch holds
-                sl.config("tma"), sl.config("ldg", flush_l2=True)]:
+                sl.config("tma"), sl.config("cpasync", k=2, copies=4), sl.config("ldg", flush_l2=True)]:
         with pytest.raises(sl.SLError) as e:
             sl.sl_run_noalloc(dev, out, dtype=sl.SL_U32, cfg=cfg)
         assert e.value.status == sl.SL_ERR_ARG
