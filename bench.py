@@ -560,7 +560,9 @@ def alloc_section(a, info) -> dict:
             "oracle": {"gbs": round(ogbs, 2), "seconds": round(osec, 2), "cores": threads,
                        "what": f"splitmix64 generation + checksum of the largest buffer ({max(sizes) >> 20} MiB; "
                                "every size's checksum is a prefix of it) on all host cores"},
-            "l2_hit_rate": "not measured in this run (ncu): see the allocation-sweep counter summary in profiles/"}
+            "l2_hit_rate": ("not measured in this run (ncu): single-pass ncu counters of the K = 2 and 8 "
+                            "endpoints at every size, profiles/ncu_counters_allocation_sweep_512mib_20gib.md, give "
+                            "DRAM reads = bytes (within 0.01%) and a derived L2 read hit rate of 0")}
 
 
 # ---- precision form (config c5 payloads, single buffers) -----------------------------

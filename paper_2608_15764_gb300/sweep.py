@@ -59,6 +59,10 @@ GPU and checked against the first cell's checksum):
        the issued counts (mismatch across K) and GB/s of the issued bytes.
   ncu-fixed  one launch per cell of the fixed-iteration control at 132 CTAs,
        K = 2 and 8, on a 2 GiB allocation (two launches).
+  ncu-alloc1  the allocation sweep's K = 2 and 8 endpoints at 512 MiB ...
+       --gib GiB, one launch each, for single-pass counter captures (DRAM
+       bytes; L1-to-L2 read sectors); --alloc-counters turns two such
+       captures into the per-size table.
   ncu-cpskew  cp.async D=4 at 256 threads with its shared-memory ring on a
        128-byte boundary and 16 bytes past one, 1 GiB (two launches).
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
@@ -179,7 +183,7 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
                 for cta in ([32 * n, 16 * n] if n % 2 == 0 else [32 * n]):
                     yield dict(mech="tma", stage_bytes=sb, stages=n, cta=cta, ring="warp", grid=0, gib=4)
     elif config == "c4":
-        for gib in (0.5, 1, 2, 4, 8, 16, 20):
+        for gib in ALLOC_GIB:
             for k in (1, 2, 4, 8, 16):
                 yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=gib)
     elif config == "ilp":
@@ -233,6 +237,15 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
             if p.copies != 1:
                 cell["copies"] = p.copies
             yield cell
+    elif config == "ncu-alloc1":
+        # the allocation sweep's K = 2 and 8 endpoints, one launch each, at the
+        # sizes up to --gib; captured only with metric sets that ncu collects
+        # in a single pass (no device-memory save and restore between
+        # passes), the only kind taken on full-size buffers
+        for g in ALLOC_GIB:
+            if g <= gib:
+                for k in (2, 8):
+                    yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=g)
     elif config == "ncu-cpskew":
         for skew in (0, 1):
             yield dict(mech="cpasync", k=4, cta=256, grid=0, skew=skew, gib=1)
@@ -243,6 +256,44 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
             yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=1)
     else:
         raise ValueError(config)
+
+
+ALLOC_GIB = (0.5, 1, 2, 4, 8, 16, 20)
+
+
+def alloc_counter_table(dram_csv: str, l2_csv: str, gib: float) -> list[dict]:
+    """Rows of the allocation sweep's single-pass counters: `ncu-alloc1` run
+    twice under ncu, once for dram__bytes_read.sum / dram__bytes_write.sum and
+    once for lts__t_sectors_srcunit_tex_op_read.sum / lts__t_sectors.sum (each
+    set takes one pass; together they take more).  Launch i of a capture is
+    cell i of the configuration.  The L2 hit rate of the kernel's reads is
+    derived as 1 - DRAM read bytes / (32 x L1-to-L2 read sectors): the share
+    of requested sectors that needed no DRAM read (the per-request hit and
+    miss counters take three passes)."""
+    cells = [c for c in _cells("ncu-alloc1", 1, gib=gib)]
+    per = {}
+    for path in (dram_csv, l2_csv):
+        for r in read_ncu_csv(path):
+            if r["unit"] not in ("byte", "sector", ""):
+                raise ValueError(f"{path}: {r['metric']} in {r['unit']}; capture with --print-units base")
+            per.setdefault(path, {}).setdefault(r["id"], {})[r["metric"]] = r["value"]
+    ids = {path: sorted(v) for path, v in per.items()}
+    for path in (dram_csv, l2_csv):
+        if len(ids.get(path, [])) != len(cells):
+            raise ValueError(f"{path}: {len(ids.get(path, []))} launches for {len(cells)} cells")
+    rows = []
+    for i, c in enumerate(cells):
+        d = per[dram_csv][ids[dram_csv][i]]
+        l2 = per[l2_csv][ids[l2_csv][i]]
+        nbytes = int(c["gib"] * (1 << 30)) // 16 * 16
+        req = 32.0 * l2["lts__t_sectors_srcunit_tex_op_read.sum"]
+        rows.append({"gib": c["gib"], "k": c["k"], "bytes": nbytes,
+                     "dram_read": d["dram__bytes_read.sum"], "dram_write": d["dram__bytes_write.sum"],
+                     "dram_read_over_bytes": round(d["dram__bytes_read.sum"] / nbytes, 7),
+                     "l1_l2_read_sectors": l2["lts__t_sectors_srcunit_tex_op_read.sum"],
+                     "l2_sectors": l2["lts__t_sectors.sum"],
+                     "l2_read_hit_derived": float(f"{1.0 - d['dram__bytes_read.sum'] / req:.4g}") if req else None})
+    return rows
 
 
 def _expected_loads(mech: str, nbytes: int, passes: int) -> int:
@@ -682,9 +733,13 @@ def main(argv=None):
     ap.add_argument("--traffic", nargs="+", default=None, metavar="SPEC=CSV",
                     help="write --traffic-out from single-launch ncu-point captures instead of running a sweep")
     ap.add_argument("--traffic-out", default=os.path.join("profiles", "traffic.json"))
+    ap.add_argument("--alloc-counters", nargs=2, default=None, metavar=("DRAM_CSV", "L2_CSV"),
+                    help="print the allocation sweep's single-pass counter table from two ncu-alloc1 captures "
+                         "(sizes up to --gib) instead of running a sweep")
     ap.add_argument("--config", required=False,
                     choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "cpgroups", "c3", "c4", "ilp", "primary",
-                             "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "l2", "cpratio", "ladder", "k1gate", "two",
+                             "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "ncu-alloc1", "l2", "cpratio", "ladder",
+                             "k1gate", "two",
                              "launches"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--repeats", type=int, default=10)
@@ -695,6 +750,10 @@ def main(argv=None):
                     help="fold of every cell (the buffer holds splitmix64 bits whatever the dtype: for float "
                          "dtypes only timing and counters mean anything, the float sums do not)")
     a = ap.parse_args(argv)
+    if a.alloc_counters:
+        for row in alloc_counter_table(a.alloc_counters[0], a.alloc_counters[1], gib=a.gib):
+            print(json.dumps(row), flush=True)
+        return 0
     if a.traffic:
         doc = write_traffic(a.traffic, a.traffic_out, gib=a.gib)
         print(json.dumps({"traffic_points": len(doc["points"]), "out": a.traffic_out}), flush=True)

@@ -188,3 +188,34 @@ def test_traffic_writer_reads_single_launch_captures(tmp_path):
                               row(1, "dram__bytes_read.sum", "byte", "1"), row(1, "dram__bytes_write.sum", "byte", "1")]))
     with pytest.raises(ValueError):
         sweep.write_traffic([f"ldgdyn:4:256={two}"], str(out))
+
+
+def test_alloc_counter_table_pairs_launches_with_cells(tmp_path):
+    """The allocation sweep's single-pass counters: launch i of each capture is
+    cell i (K = 2 and 8 per size, ascending); the derived L2 read hit rate is
+    1 - DRAM read bytes / (32 x L1-to-L2 read sectors)."""
+    from paper_2608_15764_gb300 import sweep
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+           '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+
+    def row(i, metric, unit, value):
+        return (f'"{i}","1","python","h","void sl::k_ldg<2, 256, 0, 0, 0>(sl::KArgs)","1","7","(256, 1, 1)",'
+                f'"(608, 1, 1)","0","10.3","","{metric}","{unit}","{value}"')
+
+    cells = [(g, k) for g in (0.5, 1) for k in (2, 8)]
+    dram, l2 = [hdr], [hdr]
+    for i, (g, k) in enumerate(cells):
+        nbytes = int(g * (1 << 30))
+        dram += [row(i, "dram__bytes_read.sum", "byte", nbytes - 32 * 10 * (i + 1)),
+                 row(i, "dram__bytes_write.sum", "byte", 3000000)]
+        l2 += [row(i, "lts__t_sectors_srcunit_tex_op_read.sum", "sector", nbytes // 32),
+               row(i, "lts__t_sectors.sum", "sector", nbytes // 32 * 3 // 2)]
+    (tmp_path / "d.csv").write_text("\n".join(dram) + "\n")
+    (tmp_path / "l.csv").write_text("\n".join(l2) + "\n")
+    rows = sweep.alloc_counter_table(str(tmp_path / "d.csv"), str(tmp_path / "l.csv"), gib=1)
+    assert [(r["gib"], r["k"]) for r in rows] == cells
+    r = rows[3]
+    assert r["bytes"] == 1 << 30 and r["dram_read"] == (1 << 30) - 1280
+    assert r["l2_read_hit_derived"] == pytest.approx(1280 / (1 << 30), rel=1e-3)
+    with pytest.raises(ValueError):  # a capture with a launch missing
+        sweep.alloc_counter_table(str(tmp_path / "d.csv"), str(tmp_path / "l.csv"), gib=2)
