@@ -145,8 +145,10 @@ def test_tune_points_specs_loads_and_choice():
 
 
 def test_counter_capture_configs_stay_small():
-    """Every counter-capture configuration is one or two launches on at most
-    2 GiB (the capture-size rule for multi-pass ncu runs)."""
+    """Every counter-capture configuration for multi-pass metric sets is one or
+    two launches on at most 2 GiB (the capture-size rule); ncu-alloc1, the
+    one that reaches 20 GiB, is for single-pass metric sets and runs one
+    launch per cell."""
     from paper_2608_15764_gb300 import sweep
     sms = 152
     for cfg, kw in [("ncu-primary", {}), ("ncu-fixed", {}), ("ncu-cpskew", {}), ("ncu-point", {"point": "ldgdyn:2:512"}),
@@ -157,6 +159,9 @@ def test_counter_capture_configs_stay_small():
     assert (w["mech"], w["ring"], w["stages"], w["cta"]) == ("tma", "warp", 8, 256)
     with pytest.raises(ValueError):
         list(sweep._cells("ncu-alloc", sms))
+    a = list(sweep._cells("ncu-alloc1", sms, gib=20))
+    assert [(c["gib"], c["k"]) for c in a] == [(g, k) for g in sweep.ALLOC_GIB for k in (2, 8)]
+    assert len(list(sweep._cells("ncu-alloc1", sms))) == 4  # default --gib 1: 512 MiB and 1 GiB
 
 
 def test_traffic_writer_reads_single_launch_captures(tmp_path):
