@@ -61,8 +61,11 @@ GPU and checked against the first cell's checksum):
        K = 2 and 8, on a 2 GiB allocation (two launches).
   ncu-alloc1  the allocation sweep's K = 2 and 8 endpoints at 512 MiB ...
        --gib GiB, one launch each, for single-pass counter captures (DRAM
-       bytes; L1-to-L2 read sectors); --alloc-counters turns two such
-       captures into the per-size table.
+       bytes; L1-to-L2 read sectors); --counter-table turns two such
+       captures into the per-cell table.
+  ncu-c2  the residency grid's K sweep (K <= 8) at 1,024 threads per SM (CTA
+       128 x 8, 256 x 4, 512 x 2 and 1,024 x 1) on 4 GiB, one launch each, for
+       the same single-pass captures.
   ncu-cpskew  cp.async D=4 at 256 threads with its shared-memory ring on a
        128-byte boundary and 16 bytes past one, 1 GiB (two launches).
   k1gate  paper §4.1's streaming-read qualification row: 4-byte plain loads
@@ -246,6 +249,16 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
             if g <= gib:
                 for k in (2, 8):
                     yield dict(mech="ldg", k=k, cta=256, grid=4 * sms, gib=g)
+    elif config == "ncu-c2":
+        # the residency grid's K sweep at 1,024 threads per SM (CTA 128 x 8,
+        # 256 x 4, 512 x 2 resident CTAs, and the paper's primary 1,024 x 1) on
+        # 4 GiB, one launch per cell: for single-pass counter captures, as
+        # ncu-alloc1
+        # (K = 12 and 16 need more than 64 registers per thread, so they never
+        # run at 1,024 threads per SM)
+        for cta, r in ((128, 8), (256, 4), (512, 2), (1024, 1)):
+            for k in (1, 2, 3, 4, 6, 8):
+                yield dict(mech="ldg", k=k, cta=cta, grid=r * sms, resident_req=r, gib=4)
     elif config == "ncu-cpskew":
         for skew in (0, 1):
             yield dict(mech="cpasync", k=4, cta=256, grid=0, skew=skew, gib=1)
@@ -261,16 +274,19 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
 ALLOC_GIB = (0.5, 1, 2, 4, 8, 16, 20)
 
 
-def alloc_counter_table(dram_csv: str, l2_csv: str, gib: float) -> list[dict]:
-    """Rows of the allocation sweep's single-pass counters: `ncu-alloc1` run
+def counter_table(config: str, dram_csv: str, l2_csv: str, gib: float = 20.0) -> list[dict]:
+    """Rows of a single-pass counter configuration (ncu-alloc1, ncu-c2) run
     twice under ncu, once for dram__bytes_read.sum / dram__bytes_write.sum and
     once for lts__t_sectors_srcunit_tex_op_read.sum / lts__t_sectors.sum (each
     set takes one pass; together they take more).  Launch i of a capture is
-    cell i of the configuration.  The L2 hit rate of the kernel's reads is
-    derived as 1 - DRAM read bytes / (32 x L1-to-L2 read sectors): the share
-    of requested sectors that needed no DRAM read (the per-request hit and
-    miss counters take three passes)."""
-    cells = [c for c in _cells("ncu-alloc1", 1, gib=gib)]
+    cell i of the configuration (cells that are infeasible on the device
+    launch nothing: capture on a GPU where every cell runs).  The L2 hit rate
+    of the kernel's reads is derived as 1 - DRAM read bytes / (32 x L1-to-L2
+    read sectors): the share of requested sectors that needed no DRAM read
+    (the per-request hit and miss counters take three passes)."""
+    if config not in ("ncu-alloc1", "ncu-c2"):
+        raise ValueError(f"{config} is not a single-pass counter configuration")
+    cells = [c for c in _cells(config, 1, gib=gib)]
     per = {}
     for path in (dram_csv, l2_csv):
         for r in read_ncu_csv(path):
@@ -287,7 +303,7 @@ def alloc_counter_table(dram_csv: str, l2_csv: str, gib: float) -> list[dict]:
         l2 = per[l2_csv][ids[l2_csv][i]]
         nbytes = int(c["gib"] * (1 << 30)) // 16 * 16
         req = 32.0 * l2["lts__t_sectors_srcunit_tex_op_read.sum"]
-        rows.append({"gib": c["gib"], "k": c["k"], "bytes": nbytes,
+        rows.append({"gib": c["gib"], "k": c["k"], "cta": c["cta"], "resident": c.get("resident_req"), "bytes": nbytes,
                      "dram_read": d["dram__bytes_read.sum"], "dram_write": d["dram__bytes_write.sum"],
                      "dram_read_over_bytes": round(d["dram__bytes_read.sum"] / nbytes, 7),
                      "l1_l2_read_sectors": l2["lts__t_sectors_srcunit_tex_op_read.sum"],
@@ -733,12 +749,13 @@ def main(argv=None):
     ap.add_argument("--traffic", nargs="+", default=None, metavar="SPEC=CSV",
                     help="write --traffic-out from single-launch ncu-point captures instead of running a sweep")
     ap.add_argument("--traffic-out", default=os.path.join("profiles", "traffic.json"))
-    ap.add_argument("--alloc-counters", nargs=2, default=None, metavar=("DRAM_CSV", "L2_CSV"),
-                    help="print the allocation sweep's single-pass counter table from two ncu-alloc1 captures "
-                         "(sizes up to --gib) instead of running a sweep")
+    ap.add_argument("--counter-table", nargs=2, default=None, metavar=("DRAM_CSV", "L2_CSV"),
+                    help="print the per-cell table of two single-pass captures of --config (ncu-alloc1 with "
+                         "sizes up to --gib, or ncu-c2) instead of running a sweep")
     ap.add_argument("--config", required=False,
                     choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "cpgroups", "c3", "c4", "ilp", "primary",
-                             "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "ncu-alloc1", "l2", "cpratio", "ladder",
+                             "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "ncu-alloc1", "ncu-c2", "l2", "cpratio",
+                             "ladder",
                              "k1gate", "two",
                              "launches"])
     ap.add_argument("--out", default=None)
@@ -750,8 +767,8 @@ def main(argv=None):
                     help="fold of every cell (the buffer holds splitmix64 bits whatever the dtype: for float "
                          "dtypes only timing and counters mean anything, the float sums do not)")
     a = ap.parse_args(argv)
-    if a.alloc_counters:
-        for row in alloc_counter_table(a.alloc_counters[0], a.alloc_counters[1], gib=a.gib):
+    if a.counter_table:
+        for row in counter_table(a.config, a.counter_table[0], a.counter_table[1], gib=a.gib):
             print(json.dumps(row), flush=True)
         return 0
     if a.traffic:

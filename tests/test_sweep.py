@@ -162,6 +162,8 @@ def test_counter_capture_configs_stay_small():
     a = list(sweep._cells("ncu-alloc1", sms, gib=20))
     assert [(c["gib"], c["k"]) for c in a] == [(g, k) for g in sweep.ALLOC_GIB for k in (2, 8)]
     assert len(list(sweep._cells("ncu-alloc1", sms))) == 4  # default --gib 1: 512 MiB and 1 GiB
+    c2 = list(sweep._cells("ncu-c2", sms))
+    assert len(c2) == 4 * 6 and all(c["gib"] == 4 and c["cta"] * c["resident_req"] == 1024 for c in c2)
 
 
 def test_traffic_writer_reads_single_launch_captures(tmp_path):
@@ -217,10 +219,12 @@ def test_alloc_counter_table_pairs_launches_with_cells(tmp_path):
                row(i, "lts__t_sectors.sum", "sector", nbytes // 32 * 3 // 2)]
     (tmp_path / "d.csv").write_text("\n".join(dram) + "\n")
     (tmp_path / "l.csv").write_text("\n".join(l2) + "\n")
-    rows = sweep.alloc_counter_table(str(tmp_path / "d.csv"), str(tmp_path / "l.csv"), gib=1)
+    rows = sweep.counter_table("ncu-alloc1", str(tmp_path / "d.csv"), str(tmp_path / "l.csv"), gib=1)
     assert [(r["gib"], r["k"]) for r in rows] == cells
     r = rows[3]
     assert r["bytes"] == 1 << 30 and r["dram_read"] == (1 << 30) - 1280
     assert r["l2_read_hit_derived"] == pytest.approx(1280 / (1 << 30), rel=1e-3)
     with pytest.raises(ValueError):  # a capture with a launch missing
-        sweep.alloc_counter_table(str(tmp_path / "d.csv"), str(tmp_path / "l.csv"), gib=2)
+        sweep.counter_table("ncu-alloc1", str(tmp_path / "d.csv"), str(tmp_path / "l.csv"), gib=2)
+    with pytest.raises(ValueError):  # not a single-pass configuration
+        sweep.counter_table("c1", str(tmp_path / "d.csv"), str(tmp_path / "l.csv"))
