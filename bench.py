@@ -560,9 +560,30 @@ def alloc_section(a, info) -> dict:
             "oracle": {"gbs": round(ogbs, 2), "seconds": round(osec, 2), "cores": threads,
                        "what": f"splitmix64 generation + checksum of the largest buffer ({max(sizes) >> 20} MiB; "
                                "every size's checksum is a prefix of it) on all host cores"},
-            "l2_hit_rate": ("not measured in this run (ncu): single-pass ncu counters of the K = 2 and 8 "
-                            "endpoints at every size, profiles/ncu_counters_allocation_sweep_512mib_20gib.md, give "
-                            "DRAM reads = bytes (within 0.01%) and a derived L2 read hit rate of 0")}
+            "l2_hit_rate": _alloc_counters(sizes)}
+
+
+def _alloc_counters(sizes) -> dict:
+    """The allocation sweep's L2 read hit rate and DRAM reads per size and K
+    endpoint, from the committed single-pass ncu captures of the same kernels
+    (profiles/alloc_counters.json; ncu never runs inside the benchmark), or a
+    note when the kernels' code has changed since."""
+    path = os.path.join(ROOT, "profiles", "alloc_counters.json")
+    try:
+        doc = json.load(open(path))
+    except Exception:
+        return {"note": "no profiles/alloc_counters.json"}
+    if doc.get("kernel_source_hash") != kernel_source_hash():
+        return {"note": "kernels changed since the counters were taken"}
+    per = {}
+    for r in doc["rows"]:
+        if r["bytes"] in sizes:
+            per.setdefault(str(r["bytes"]), {})[f"k{r['k']}"] = {
+                "l2_read_hit_derived": r["l2_read_hit_derived"], "dram_read_over_bytes": r["dram_read_over_bytes"],
+                "l2_sectors_over_bytes": round(32 * r["l2_sectors"] / r["bytes"], 4)}
+    return {"source": "profiles/alloc_counters.json, single-pass ncu captures of the K = 2 and 8 endpoints "
+                      "(1 - DRAM read bytes / requested sectors x 32; the hit/miss counters take 3 passes)",
+            "command": doc.get("command"), "per_size": per}
 
 
 # ---- precision form (config c5 payloads, single buffers) -----------------------------

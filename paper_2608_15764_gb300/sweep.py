@@ -752,6 +752,9 @@ def main(argv=None):
     ap.add_argument("--counter-table", nargs=2, default=None, metavar=("DRAM_CSV", "L2_CSV"),
                     help="print the per-cell table of two single-pass captures of --config (ncu-alloc1 with "
                          "sizes up to --gib, or ncu-c2) instead of running a sweep")
+    ap.add_argument("--counter-out", default=None,
+                    help="with --counter-table: also write the table with the kernel code hash as JSON "
+                         "(profiles/alloc_counters.json is read by bench.py's allocation sweep)")
     ap.add_argument("--config", required=False,
                     choices=["c1", "c2", "c2w", "c2fixed", "fixedit", "cpskew", "cpgroups", "c3", "c4", "ilp", "primary",
                              "ncu-point", "ncu-primary", "ncu-fixed", "ncu-cpskew", "ncu-alloc1", "ncu-c2", "l2", "cpratio",
@@ -768,8 +771,19 @@ def main(argv=None):
                          "dtypes only timing and counters mean anything, the float sums do not)")
     a = ap.parse_args(argv)
     if a.counter_table:
-        for row in counter_table(a.config, a.counter_table[0], a.counter_table[1], gib=a.gib):
+        rows = counter_table(a.config, a.counter_table[0], a.counter_table[1], gib=a.gib)
+        for row in rows:
             print(json.dumps(row), flush=True)
+        if a.counter_out:
+            from .build import kernel_source_hash
+            doc = {"kernel_source_hash": kernel_source_hash(), "config": a.config, "gib": a.gib,
+                   "command": f"python -m paper_2608_15764_gb300.sweep --repeats 1 --config {a.config} --gib {a.gib:g} "
+                              "under ncu twice: --metrics dram__bytes_read.sum,dram__bytes_write.sum and --metrics "
+                              "lts__t_sectors_srcunit_tex_op_read.sum,lts__t_sectors.sum (--print-units base "
+                              "--clock-control none -k regex:k_ldg --csv), both single-pass",
+                   "rows": rows}
+            with open(a.counter_out, "w") as f:
+                json.dump(doc, f, indent=1)
         return 0
     if a.traffic:
         doc = write_traffic(a.traffic, a.traffic_out, gib=a.gib)

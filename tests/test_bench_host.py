@@ -43,3 +43,19 @@ def test_kernel_hash_ignores_comments_only():
     assert build._code_only(a) == build._code_only(b)
     assert build._code_only(a) != build._code_only(c)
     assert len(build.kernel_source_hash()) == 16
+
+
+def test_alloc_counters_match_the_sweep_sizes():
+    """The committed single-pass allocation counters cover every size of the
+    benchmark's allocation sweep at both K endpoints, for the current kernels."""
+    import bench
+    sizes = [int(g * (1 << 30)) for g in (0.5, 1, 2, 4, 8, 16, 20)]
+    r = bench._alloc_counters(sizes)
+    if r.get("note") == "kernels changed since the counters were taken":
+        pytest.skip("the allocation counters were taken on another version of the kernels' code")
+    assert "note" not in r, r
+    assert sorted(int(b) for b in r["per_size"]) == sizes
+    for per_k in r["per_size"].values():
+        assert set(per_k) == {"k2", "k8"}
+        for v in per_k.values():
+            assert abs(v["dram_read_over_bytes"] - 1) < 1e-3 and abs(v["l2_read_hit_derived"]) < 1e-3
