@@ -59,3 +59,22 @@ def test_alloc_counters_match_the_sweep_sizes():
         assert set(per_k) == {"k2", "k8"}
         for v in per_k.values():
             assert abs(v["dram_read_over_bytes"] - 1) < 1e-3 and abs(v["l2_read_hit_derived"]) < 1e-3
+
+
+def test_traffic_counters_name_catalogue_points():
+    """profiles/traffic.json: every captured point is a point of the benchmark's
+    catalogue (its label is what bench.py looks up), with DRAM reads within
+    0.1% of the bytes, and the benchmark's usual choices are among them."""
+    import json
+    from paper_2608_15764_gb300 import tune
+    from paper_2608_15764_gb300.build import kernel_source_hash
+    doc = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    if doc["kernel_source_hash"] != kernel_source_hash():
+        pytest.skip("the traffic counters were taken on another version of the kernels' code")
+    labels = {p.label() for p in tune.default_points()}
+    assert set(doc["points"]) <= labels
+    for e in doc["points"].values():
+        assert abs(e["dram_read"] / e["bytes"] - 1) < 1e-3
+        assert tune.parse_point(e["spec"]).label() in doc["points"]
+    for spec in ("ldgdyn:4:512", "ldgdyn:4:256", "ldg32dyn:2:256"):
+        assert tune.parse_point(spec).label() in doc["points"]
