@@ -78,3 +78,17 @@ def test_traffic_counters_name_catalogue_points():
         assert tune.parse_point(e["spec"]).label() in doc["points"]
     for spec in ("ldgdyn:4:512", "ldgdyn:4:256", "ldg32dyn:2:256"):
         assert tune.parse_point(spec).label() in doc["points"]
+
+
+def test_counter_files_from_other_kernels_are_not_reported(tmp_path, monkeypatch):
+    """Counters taken on another version of the kernels' code are reported as
+    such (a note, no numbers), and a missing file is noted too."""
+    import json
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._alloc_counters([1 << 30]) == {"note": "no profiles/alloc_counters.json"}
+    assert bench._traffic("ldg K=4 cta=512 cop=0 dyn", 4 << 30) == (None, "no profiles/traffic.json")
+    (tmp_path / "profiles" / "alloc_counters.json").write_text(json.dumps({"kernel_source_hash": "0", "rows": []}))
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"kernel_source_hash": "0", "points": {}}))
+    assert bench._alloc_counters([1 << 30]) == {"note": "kernels changed since the counters were taken"}
+    assert bench._traffic("ldg K=4 cta=512 cop=0 dyn", 4 << 30)[0] is None
