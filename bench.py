@@ -594,6 +594,7 @@ PREC_CELLS = ([dict(mech="ldg", k=k, cta=256) for k in (1, 2, 4, 8, 16)] +
               [dict(mech="ldg32", k=k, cta=256, order="dyn") for k in (2, 6)] +
               [dict(mech="cpasync", k=d, cta=256) for d in (2, 4, 6)] +
               [dict(mech="cpasync", k=d, copies=g, cta=256) for d, g in ((2, 2), (2, 8))] +
+              [dict(mech="cpasync", k=d, copies=g, cta=256, order="dyn") for d, g in ((4, 1), (2, 8))] +
               [dict(mech="tma", stage_bytes=sb, stages=n, cta=256) for sb, n in ((16384, 2), (16384, 4), (65536, 2))] +
               [dict(mech="tma", stage_bytes=sb, stages=n, cta=32 * n, ring="warp")
                for sb, n in ((4096, 6), (4096, 8), (16384, 8))])

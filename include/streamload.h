@@ -84,9 +84,9 @@ typedef enum { SL_U32 = 0, SL_F32 = 1, SL_BF16 = 2, SL_FP8_E4M3 = 3 } sl_dtype;
 typedef enum { SL_LDG = 0, SL_CPASYNC = 1, SL_TMA = 2, SL_LDSTS = 3, SL_LDG4 = 4, SL_LDG32 = 5 } sl_mech;
 /* Traversal of the buffer by the CTAs.  SL_ASC / SL_DESC: CTA b takes tiles
  * b, b+grid, ... from the first (or last) tile on (the paper's layout).
- * SL_DYN (SL_LDG and SL_LDG32): CTAs claim contiguous chunks of about 1 MiB from an
- * atomic counter; integer results are exact, float sums meet the same bound
- * but are not bit-reproducible between runs. */
+ * SL_DYN (SL_LDG, SL_LDG32 and SL_CPASYNC): CTAs claim contiguous chunks of
+ * about 1 MiB from an atomic counter; integer results are exact, float sums
+ * meet the same bound but are not bit-reproducible between runs. */
 typedef enum { SL_ASC = 0, SL_DESC = 1, SL_DYN = 2 } sl_order;
 /* LDG load flavour: SL_COP_CG is the paper's primary cell (ld.global.cg,
  * §4.2); the other two ask L2 for 256-byte prefetch granules. */

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               f"-I{os.path.join(ROOT, 'include')}"]
 CU_SOURCES = ["api.cu", "k_util.cu", "k_ldg_u32.cu", "k_ldg_f32.cu", "k_ldg_bf16.cu", "k_ldg_fp8.cu",
-              "k_cpasync.cu", "k_cpasync_g.cu", "k_tma.cu", "noalloc.cu", "k_batch_ldg.cu", "k_batch_misc.cu", "batch_api.cu",
+              "k_cpasync.cu", "k_cpasync_g.cu", "k_cpasync_dyn.cu", "k_tma.cu", "noalloc.cu", "k_batch_ldg.cu", "k_batch_misc.cu", "batch_api.cu",
               "k_ldg_dyn.cu", "k_ldsts.cu", "k_chase.cu", "k_ldg4.cu", "k_two.cu", "k_ldg32.cu", "k_ldg_fixed.cu", "k_cov.cu"]
 HEADERS = ["sl_internal.h", "sl_device.cuh", "sl_mbar.cuh", "k_ldg.cuh", "k_batch.cuh", "k_cpasync.cuh",
            os.path.join("..", "..", "include", "streamload.h")]

@@ -237,8 +237,8 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     const bool dyn = cfg->order == SL_DYN;
     const bool fixed = cfg->target_loads > 0;
     if (fixed && cfg->mech != SL_LDG) return fail(SL_ERR_ARG, "the fixed-iteration control is implemented for SL_LDG");
-    if (dyn && ((cfg->mech != SL_LDG && cfg->mech != SL_LDG32) || cfg->cop != SL_COP_CG))
-        return fail(SL_ERR_ARG, "the SL_DYN traversal is implemented for SL_LDG / SL_LDG32 with SL_COP_CG");
+    if (dyn && ((cfg->mech != SL_LDG && cfg->mech != SL_LDG32 && cfg->mech != SL_CPASYNC) || cfg->cop != SL_COP_CG))
+        return fail(SL_ERR_ARG, "the SL_DYN traversal is implemented for SL_LDG / SL_LDG32 / SL_CPASYNC with SL_COP_CG");
     const uint64_t passes = cfg->passes == 0 ? 1 : static_cast<uint64_t>(cfg->passes);
     const int cta = cfg->cta;
     if (cta < 32 || cta > 1024 || (cta & 31)) return fail(SL_ERR_ARG, "cta %d not a multiple of 32 in 32..1024", cta);
@@ -315,11 +315,19 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
             return fail(SL_ERR_ARG, "cp.async copies per commit group %d not in {1, 2, 4, 8}", g);
         if (cfg->k * g > SL_MAX_D)
             return fail(SL_ERR_ARG, "cp.async D x G = %d x %d copies in flight exceeds %d", cfg->k, g, SL_MAX_D);
-        p->fn = cfg->mech == SL_CPASYNC ? sl::cpasync_kernel(dtype, cfg->k, g) : sl::ldsts_kernel(dtype, cfg->k);
+        if (cfg->mech == SL_CPASYNC && dyn) {
+            p->fn = sl::cpasync_dyn_kernel(dtype, cfg->k, g);
+            if (!p->fn)
+                return fail(SL_ERR_ARG, "no SL_DYN cp.async kernel for D %d x G %d (D 1/2/3/4/6/8 with one copy per "
+                            "group; D x G 2 x 2, 1 x 4, 2 x 4, 1 x 8, 2 x 8)", cfg->k, g);
+        } else {
+            p->fn = cfg->mech == SL_CPASYNC ? sl::cpasync_kernel(dtype, cfg->k, g) : sl::ldsts_kernel(dtype, cfg->k);
+        }
         p->block = cta;
         p->smem = static_cast<size_t>(cfg->k) * g * cta * 16 +
                   (((cfg->debug_flags >> SL_DEBUG_SMEM_SKEW_SHIFT) & 7) ? 128 : 0);  // room for a skewed ring
         tile_vec = static_cast<uint64_t>(cta) * cfg->k * g;
+        if (dyn) tile_vec *= std::max<uint64_t>(1, DYN_CHUNK_VEC / tile_vec);  // chunk of ~1 MiB
         p->warps = cta / 32;
         break;
     }
@@ -399,8 +407,9 @@ int make_plan(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, const s
     // TMA ring's chunk index runs up to total + stages * grid).
     const uint64_t total = ntiles * passes;
     const uint64_t per_thread = ((total + grid - 1) / grid) * ((tile_vec + cta - 1) / cta);
+    // (SL_DYN counters run up to three claims per CTA past the last chunk)
     const uint64_t ahead = static_cast<uint64_t>(grid) *
-                           ((cfg->mech == SL_TMA && cfg->tma_ring == SL_RING_WARP) ? cfg->stages : 1);
+                           ((cfg->mech == SL_TMA && cfg->tma_ring == SL_RING_WARP) ? cfg->stages : dyn ? 3 : 1);
     if (total + ahead >= (1ull << 32) || per_thread >= (1ull << 32))
         return fail(SL_ERR_ARG, "passes x tiles too large for one launch (%llu tiles); lower passes",
                     (unsigned long long)total);
@@ -458,7 +467,9 @@ const void* coverage_fn(const sl_config* cfg) {
         if (cfg->target_loads) return sl::ldg_fixed_cov_kernel(cfg->k, cfg->cta);
         return cfg->cop == SL_COP_CG ? sl::ldg_cov_kernel(cfg->k, cfg->cta, dyn) : nullptr;
     case SL_LDG32: return sl::ldg32_cov_kernel(cfg->k, cfg->cta, dyn);
-    case SL_CPASYNC: return sl::cpasync_cov_kernel(cfg->k, copies_per_group(cfg));
+    case SL_CPASYNC:
+        return dyn ? sl::cpasync_dyn_cov_kernel(cfg->k, copies_per_group(cfg))
+                   : sl::cpasync_cov_kernel(cfg->k, copies_per_group(cfg));
     case SL_LDSTS: return sl::ldsts_cov_kernel(cfg->k);
     case SL_TMA: return cfg->tma_ring == SL_RING_WARP ? sl::tma_warp_cov_kernel() : sl::tma_cov_kernel(tma_batch(cfg));
     default: return nullptr;
@@ -477,7 +488,8 @@ int enqueue_locked(DevCtx* c, const void* buf, uint64_t bytes, int32_t dtype, co
         if (!fn)
             return fail(SL_ERR_ARG, "no coverage instantiation for this configuration (uint32; LDG K 1/3/8/16 "
                         "grid-stride or 2/12 SL_DYN at cta 128/256/512; SL_LDG32 K 1/3/8 at cta 256; "
-                        "fixed-iteration K 2/8 at cta 256/1024; cp.async D 1/4/16, D x G 2 x 4 and 3 x 2; SL_LDSTS G 1/16; TMA)");
+                        "fixed-iteration K 2/8 at cta 256/1024; cp.async D 1/4/16, D x G 2 x 4 and 3 x 2, SL_DYN D 4 and 2 x 4; "
+                        "SL_LDSTS G 1/16; TMA)");
         FuncInfo* fi = nullptr;
         rc = func_info(c, fn, p.smem, &fi);
         if (rc) return rc;

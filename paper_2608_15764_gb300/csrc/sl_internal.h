@@ -56,6 +56,7 @@ enum : uint32_t { DEV_ERR_NONE = 0, DEV_ERR_TIMEOUT_FULL = 1, DEV_ERR_TIMEOUT_EM
 const void* ldg_kernel(int dtype, int k, int cta, int cop);
 const void* ldg_dyn_kernel(int dtype, int k, int cta);
 const void* cpasync_kernel(int dtype, int d, int g);  // g: copies per commit group
+const void* cpasync_dyn_kernel(int dtype, int d, int g);  // SL_DYN traversal
 const void* ldsts_kernel(int dtype, int g);
 // SL_RING_CTA: batch = vectors a consumer thread reads into registers at a
 // time (4, or 1 where a thread reads fewer than 4 vectors of a stage)
@@ -75,6 +76,7 @@ const void* ldg_cov_kernel(int k, int cta, bool dyn);
 const void* ldg32_cov_kernel(int k, int cta, bool dyn);
 const void* ldg_fixed_cov_kernel(int k, int cta);
 const void* cpasync_cov_kernel(int d, int g);
+const void* cpasync_dyn_cov_kernel(int d, int g);
 const void* ldsts_cov_kernel(int g);
 const void* tma_cov_kernel(int batch);
 const void* tma_warp_cov_kernel();

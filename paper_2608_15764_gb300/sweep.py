@@ -27,7 +27,8 @@ GPU and checked against the first cell's checksum):
        CTA per SM), on 1 GiB.
   cpgroups  cp.async with G in {1,2,4,8} 16-byte copies per commit group
        and D groups in flight (D*G <= 16): every cell at 256 threads on
-       4 GiB, and one warp (32 threads, one CTA) on 32 MiB.
+       4 GiB, one warp (32 threads, one CTA) on 32 MiB, and the eleven
+       dynamic-chunk instantiations at 256 threads on 4 GiB.
   ladder  paper §4.1: pointer-chase latency versus footprint, .ca / .cg.
   l2   the L2-targeted backend (paper §4.2 "L2-targeted control"): 16, 32
        and 64 MiB buffers (below the 129 MB L2) read 4 GiB / size passes per
@@ -205,6 +206,9 @@ def _cells(config: str, sms: int, point: str | None = None, gib: float = 1.0):
             for d in (1, 2, 4, 8, 16):
                 if d * g <= 16:
                     yield dict(mech="cpasync", k=d, copies=g, cta=32, grid=1, gib=1 / 32)
+        # the dynamic-chunk traversal's instantiations at 256 threads
+        for d, g in ((1, 1), (2, 1), (3, 1), (4, 1), (6, 1), (8, 1), (2, 2), (1, 4), (2, 4), (1, 8), (2, 8)):
+            yield dict(mech="cpasync", k=d, copies=g, cta=256, grid=0, trav=2, gib=4)
     elif config == "primary":
         for k in (1, 2, 4, 8):
             yield dict(mech="ldg", k=k, cta=1024, grid=sms, gib=4)

@@ -87,7 +87,7 @@ class Point:
         dyn = " dyn" if self.order == 2 else ""
         if self.mech == SL_CPASYNC:
             g = f" G={self.copies}" if self.copies != 1 else ""
-            return f"cpasync D={self.k}{g} cta={self.cta}"
+            return f"cpasync D={self.k}{g} cta={self.cta}{dyn}"
         return f"{MECH_NAMES[self.mech]} K={self.k} cta={self.cta} cop={self.cop}{dyn}"
 
     def spec(self) -> str:
@@ -97,8 +97,9 @@ class Point:
         name = MECH_NAMES[self.mech] + ("dyn" if self.order == 2 else "")
         if self.mech == SL_LDG and self.order != 2:
             return f"ldg:{self.k}:{self.cta}:{self.cop}"
-        if self.mech == SL_CPASYNC and self.copies != 1:
-            return f"cpasync:{self.k}:{self.cta}:{self.copies}"
+        if self.mech == SL_CPASYNC:
+            g = f":{self.copies}" if self.copies != 1 else ""
+            return f"{name}:{self.k}:{self.cta}{g}"
         return f"{name}:{self.k}:{self.cta}"
 
     def as_dict(self) -> dict:
@@ -119,6 +120,7 @@ class Point:
 
 def parse_point(text: str) -> Point:
     """'ldg:K:cta[:cop]', 'ldgdyn:K:cta', 'ldg32:K:cta', 'ldg32dyn:K:cta', 'cpasync:D:cta[:G]',
+    'cpasyncdyn:D:cta[:G]',
     'tma:stage_bytes:stages:cta' (one ring per CTA, producer warp) or 'tmaw:stage_bytes:stages[:cta]'
     (the CTA's stages dealt to its warps; cta defaults to warp_ring_cta)."""
     f = text.split(":")
@@ -134,9 +136,9 @@ def parse_point(text: str) -> Point:
         return Point(SL_TMA, stage_bytes=int(f[1]), stages=int(f[2]), cta=int(f[3]) if len(f) > 3 else 256)
     if mech == "ldg":
         return Point(SL_LDG, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256, cop=int(f[3]) if len(f) > 3 else 0)
-    if mech == "cpasync":
+    if mech in ("cpasync", "cpasyncdyn"):
         return Point(SL_CPASYNC, k=int(f[1]), cta=int(f[2]) if len(f) > 2 else 256,
-                     copies=int(f[3]) if len(f) > 3 else 1)
+                     copies=int(f[3]) if len(f) > 3 else 1, order=2 if mech.endswith("dyn") else 0)
     raise ValueError(f"bad point {text!r}")
 
 
@@ -149,6 +151,8 @@ def warp_ring_cta(stage_bytes: int, stages: int) -> int:
 # cp.async points with several copies per commit group (D, G): the same bytes
 # in flight as D*G one-copy groups, with fewer commits and waits
 CP_GROUP_POINTS = ((1, 2), (2, 2), (1, 4), (2, 4), (1, 8))
+# cp.async under the dynamic-chunk traversal (D, G)
+CP_DYN_POINTS = ((2, 1), (3, 1), (4, 1), (6, 1), (8, 1), (1, 8), (2, 8))
 TMA_STAGE_BYTES = (4096, 16384, 65536)
 TMA_STAGES = tuple(range(2, 9))
 
@@ -156,7 +160,8 @@ TMA_STAGES = tuple(range(2, 9))
 def default_points(cta: int = 256) -> list[Point]:
     """The K-response catalogue: LDG K 1-16 (16 bytes, .cg), four .L2::256B
     points, the dynamic-chunk traversal, 32-byte loads, cp.async D 1-8 (and
-    five points with 2-8 copies per commit group), and
+    five points with 2-8 copies per commit group, and seven under the
+    dynamic-chunk traversal), and
     TMA stage sizes 4/16/64 KiB x 2-8 stages in both ring layouts (read by
     all `cta` consumer threads, and by 128 for 4 KiB stages; dealt to the
     warps, one stage per warp and, for even stage counts, two).
@@ -170,6 +175,7 @@ def default_points(cta: int = 256) -> list[Point]:
     pts += [Point(SL_LDG32, k=k, cta=cta, order=2) for k in (1, 2, 3, 4, 6, 8)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta) for d in range(1, 9)]
     pts += [Point(SL_CPASYNC, k=d, cta=cta, copies=g) for d, g in CP_GROUP_POINTS]
+    pts += [Point(SL_CPASYNC, k=d, cta=cta, copies=g, order=2) for d, g in CP_DYN_POINTS]
     pts += [Point(SL_TMA, cta=cta, stage_bytes=s, stages=n) for s in TMA_STAGE_BYTES for n in TMA_STAGES]
     # with 4 KiB stages a 256-thread CTA gives each consumer lane a single
     # 16-byte vector per stage; 128 consumer threads read two

@@ -25,6 +25,7 @@ CONFIGS = [
     ("ldg32", dict(k=3, cta=256, order="dyn")), ("ldg32", dict(k=8, cta=256, order="dyn")),
     ("cpasync", dict(k=1, cta=256)), ("cpasync", dict(k=4, cta=128)), ("cpasync", dict(k=16, cta=256)),
     ("cpasync", dict(k=2, copies=4, cta=256)), ("cpasync", dict(k=3, copies=2, cta=128, order="desc")),
+    ("cpasync", dict(k=4, cta=256, order="dyn")), ("cpasync", dict(k=2, copies=4, cta=128, order="dyn")),
     ("ldsts", dict(k=1, cta=256)), ("ldsts", dict(k=16, cta=256)),
     ("tma", dict(cta=256, stage_bytes=16384, stages=4)), ("tma", dict(cta=128, stage_bytes=4096, stages=2,
                                                                       order="desc")),

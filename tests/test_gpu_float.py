@@ -101,6 +101,12 @@ def test_cpasync_float(sl, payloads, dt, d, g):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("d,g", [(1, 1), (4, 1), (2, 4), (2, 8)])
+def test_cpasync_dynamic_float(sl, payloads, dt, d, g):
+    _check(sl, payloads[dt], dt, sl.config("cpasync", k=d, copies=g, cta=256, order="dyn"))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("stage,stages", [(4096, 4), (16384, 4), (65536, 3)])
 def test_tma_float(sl, payloads, dt, stage, stages):
     _check(sl, payloads[dt], dt, sl.config("tma", cta=256, stage_bytes=stage, stages=stages, order="desc"))

@@ -45,6 +45,7 @@ CONFIGS = [
     ("cpasync", dict(k=4, cta=256)),
     ("cpasync", dict(k=8, cta=512)),
     ("cpasync", dict(k=2, copies=4, cta=256)),
+    ("cpasync", dict(k=2, copies=8, cta=256, order="dyn")),
     ("ldsts", dict(k=4, cta=256)),
     ("tma", dict(cta=256, stage_bytes=4096, stages=2)),
     ("tma", dict(cta=256, stage_bytes=16384, stages=4, order="desc")),

@@ -165,7 +165,7 @@ def test_precision_full_size(sl, payload):
     dev = torch.from_numpy(host.view(np.uint8)).cuda()
     gate = 2e-6 * (absum if abs(ref) < 1e-3 * absum / math.sqrt(n) else abs(ref))
     for cfg in [sl.config("ldg", k=8, cta=256, order="dyn"), sl.config("cpasync", k=6, cta=256),
-                sl.config("cpasync", k=2, copies=8, cta=256),
+                sl.config("cpasync", k=2, copies=8, cta=256), sl.config("cpasync", k=2, copies=8, cta=256, order="dyn"),
                 sl.config("tma", cta=256, stage_bytes=4096, stages=8, ring="warp"), sl.config("ldg", k=8, cta=256)]:
         r = sl.sl_run(dev, dtype=dt, cfg=cfg)
         assert (r.sum_u32, r.xor_u64, r.issued_loads, r.status) == (*want, nbytes // 16, 0)

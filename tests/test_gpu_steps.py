@@ -44,6 +44,7 @@ def _results(sl, out, n):
     ("ldg", dict(k=4, cta=128), 16), ("ldg", dict(k=1, cta=1024), 16),
     ("ldg32", dict(k=4, cta=256), 32), ("ldg4", dict(k=4, cta=256), 4),
     ("cpasync", dict(k=4, cta=256), 16), ("cpasync", dict(k=2, copies=4, cta=256), 16),
+    ("cpasync", dict(k=2, copies=8, cta=256, order="dyn"), 16),
     ("ldsts", dict(k=4, cta=256), 16),
     ("ldg", dict(k=12, cta=256, order="dyn"), 16), ("ldg", dict(k=2, cta=512, order="dyn"), 16),
     ("ldg32", dict(k=6, cta=256, order="dyn"), 32),

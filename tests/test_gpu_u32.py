@@ -102,6 +102,38 @@ def test_cpasync_copies_per_group(sl, data, d, g, cta, order):
     assert r.smem_bytes == d * g * cta * 16
 
 
+CP_DYN = [(1, 1), (2, 1), (3, 1), (4, 1), (6, 1), (8, 1), (2, 2), (1, 4), (2, 4), (1, 8), (2, 8)]
+
+
+@pytest.mark.parametrize("d,g", CP_DYN)
+@pytest.mark.parametrize("cta", [32, 128, 256, 512])
+def test_cpasync_dynamic_chunks(sl, data, d, g, cta):
+    """cp.async under the SL_DYN traversal: CTAs claim ~1 MiB chunks, the
+    refills cross from one chunk into the next; every instantiated D x G."""
+    dev, _, want = data
+    _check(sl, dev, NBYTES, want, sl.config("cpasync", k=d, copies=g, cta=cta, order="dyn"))
+
+
+@pytest.mark.parametrize("grid", [1, 7, 152, 3000])
+@pytest.mark.parametrize("passes", [1, 2, 3])
+def test_cpasync_dynamic_grids_and_passes(sl, data, grid, passes):
+    dev, _, (s, x) = data
+    want = ((passes * s) % (1 << 32), x if passes % 2 else 0)
+    _check(sl, dev, NBYTES, want, sl.config("cpasync", k=4, cta=256, grid=grid, order="dyn", passes=passes),
+           passes=passes)
+
+
+def test_cpasync_dynamic_needs_an_instantiation(sl, data):
+    dev, _, _ = data
+    for kw in (dict(k=5), dict(k=4, copies=2), dict(k=16)):
+        with pytest.raises(sl.SLError) as e:
+            sl.sl_run(dev, nbytes=1024, dtype=sl.SL_U32, cfg=sl.config("cpasync", order="dyn", **kw))
+        assert e.value.status == sl.SL_ERR_ARG
+    with pytest.raises(sl.SLError) as e:
+        sl.sl_run(dev, nbytes=1024, dtype=sl.SL_U32, cfg=sl.config("ldsts", k=4, order="dyn"))
+    assert e.value.status == sl.SL_ERR_ARG
+
+
 @pytest.mark.parametrize("stage", [4096, 16384, 65536])
 @pytest.mark.parametrize("stages", [2, 3, 4, 8])
 @pytest.mark.parametrize("order", ["asc", "desc"])
@@ -188,6 +220,8 @@ def test_passes_closed_form(sl, data, mech, kw, passes):
 @pytest.mark.parametrize("nvec", [0, 1, 2, 3, 31, 33, 255, 257, 4096 + 5])
 @pytest.mark.parametrize("mech,kw", [("ldg", {"k": 1}), ("ldg", {"k": 16}), ("cpasync", {"k": 8}),
                                      ("cpasync", {"k": 1, "copies": 8}), ("cpasync", {"k": 5, "copies": 2}),
+                                     ("cpasync", {"k": 3, "order": "dyn"}),
+                                     ("cpasync", {"k": 2, "copies": 8, "order": "dyn"}),
                                      ("tma", {"stage_bytes": 4096, "stages": 2}),
                                      ("tma", {"stage_bytes": 4096, "stages": 8, "ring": "warp"}),
                                      ("tma", {"stage_bytes": 65536, "stages": 2, "ring": "warp", "cta": 32})])

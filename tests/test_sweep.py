@@ -120,9 +120,14 @@ def test_tune_points_specs_loads_and_choice():
     # per-warp point with a warp count dividing its stage count
     from paper_2608_15764_gb300 import SL_CPASYNC, SL_LDG, SL_RING_WARP, SL_TMA
     assert sorted(q.k for q in pts if q.mech == SL_LDG and q.order == 0 and q.cop == 0) == list(range(1, 17))
-    assert sorted(q.k for q in pts if q.mech == SL_CPASYNC and q.copies == 1) == list(range(1, 9))
-    assert {(q.k, q.copies) for q in pts if q.mech == SL_CPASYNC and q.copies > 1} == {(1, 2), (2, 2), (1, 4),
-                                                                                       (2, 4), (1, 8)}
+    assert sorted(q.k for q in pts if q.mech == SL_CPASYNC and q.copies == 1 and q.order == 0) == list(range(1, 9))
+    assert {(q.k, q.copies) for q in pts if q.mech == SL_CPASYNC and q.copies > 1 and q.order == 0} == \
+        {(1, 2), (2, 2), (1, 4), (2, 4), (1, 8)}
+    assert {(q.k, q.copies) for q in pts if q.mech == SL_CPASYNC and q.order == SL_DYN} == set(tune.CP_DYN_POINTS)
+    d = tune.parse_point("cpasyncdyn:2:256:8")
+    assert (d.order, d.spec(), d.label(), d.cfg().order) == (SL_DYN, "cpasyncdyn:2:256:8", "cpasync D=2 G=8 cta=256 dyn",
+                                                             SL_DYN)
+    assert tune.parse_point("cpasyncdyn:4:256").spec() == "cpasyncdyn:4:256"
     g = tune.parse_point("cpasync:2:256:4")
     assert (g.k, g.copies, g.offered, g.spec()) == (2, 4, 2 * 4 * 256 * 16, "cpasync:2:256:4")
     assert g.cfg().copies == 4 and g.label() == "cpasync D=2 G=4 cta=256" and g.as_dict()["copies"] == 4
