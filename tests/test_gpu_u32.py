@@ -354,9 +354,10 @@ def test_ldg_dynamic_ragged(sl, data, nvec):
     _check(sl, dev, nbytes, oracle.checksum(host[: nbytes // 4]), sl.config("ldg", k=4, cta=256, order="dyn"))
 
 
-def test_dynamic_rejected_outside_ldg(sl, data):
+def test_dynamic_rejected_outside_its_kernels(sl, data):
+    """SL_DYN runs on the LDG, 32-byte LDG and cp.async kernels only."""
     dev, _, _ = data
-    for cfg in [sl.config("tma", order="dyn"), sl.config("cpasync", order="dyn"),
+    for cfg in [sl.config("tma", order="dyn"), sl.config("ldsts", order="dyn"), sl.config("cpasync", k=5, order="dyn"),
                 sl.config("ldg", k=5, order="dyn"), sl.config("ldg", k=2, cop=1, order="dyn")]:
         with pytest.raises(sl.SLError) as e:
             sl.sl_run(dev, dtype=sl.SL_U32, cfg=cfg)
