@@ -168,8 +168,9 @@ def kernel_source_hash() -> str:
 
 def _traffic(label: str, nbytes: int):
     """DRAM bytes per launch of the timed kernel from profiles/traffic.json
-    (captured on a smaller buffer; DRAM traffic of this streaming kernel grows
-    in proportion to the bytes read, so it is scaled to nbytes), or None."""
+    (one captured launch per point; a capture on another size is scaled to
+    nbytes, as this streaming kernel's DRAM traffic grows in proportion to the
+    bytes read), or None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         tj = json.load(open(path))
@@ -180,8 +181,8 @@ def _traffic(label: str, nbytes: int):
     e = tj.get("points", {}).get(label)
     if not e:
         return None, f"no capture for {label}"
-    return round(e["dram_bytes_per_launch"] * nbytes / e["bytes"]), \
-        f"scaled from a {e['bytes'] >> 20} MiB capture ({tj.get('command', '')})"
+    how = "captured on the same size" if e["bytes"] == nbytes else f"scaled from a {e['bytes'] >> 20} MiB capture"
+    return round(e["dram_bytes_per_launch"] * nbytes / e["bytes"]), f"{how} ({tj.get('command', '')})"
 
 
 def host_buffer(nbytes: int, pinned: bool):

@@ -735,13 +735,13 @@ def write_traffic(pairs: list[str], out: str, gib: float = 1.0) -> dict:
             "spec": spec, "kernel": m["dram__bytes_read.sum"]["kernel"], "bytes": int(gib * (1 << 30)),
             "dram_read": int(rd), "dram_write": int(wr), "dram_bytes_per_launch": int(rd + wr)}
     doc = {"kernel_source_hash": kernel_source_hash(),
-           "command": "for each point: python -m paper_2608_15764_gb300.sweep --config ncu-point --point SPEC "
-                      "--repeats 1 > plain.log && ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
+           "command": f"for each point: python -m paper_2608_15764_gb300.sweep --config ncu-point --point SPEC "
+                      f"--gib {gib:g} --repeats 1 > plain.log && ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
                       "--print-units base --clock-control none -k regex:\"k_(ldg|tma|cpasync)\" -c 1 --csv "
                       "--log-file SPEC.csv python -m paper_2608_15764_gb300.sweep --config ncu-point --point SPEC "
-                      "--repeats 1",
+                      f"--gib {gib:g} --repeats 1 (single-pass metrics)",
            "note": f"DRAM bytes per launch on a {gib:g} GiB buffer, one captured launch per point; bench.py scales "
-                   "them to its buffer by bytes read",
+                   "them to its buffer by bytes read (a factor of 1 when the sizes match)",
            "points": points}
     with open(out, "w") as f:
         json.dump(doc, f, indent=1)
