@@ -76,7 +76,7 @@ def test_traffic_counters_name_catalogue_points():
     for e in doc["points"].values():
         assert abs(e["dram_read"] / e["bytes"] - 1) < 1e-3
         assert tune.parse_point(e["spec"]).label() in doc["points"]
-    for spec in ("ldgdyn:4:512", "ldgdyn:4:256", "ldg32dyn:2:256"):
+    for spec in ("ldgdyn:4:512", "ldgdyn:4:256", "ldgdyn:2:512", "ldg32dyn:2:256"):
         assert tune.parse_point(spec).label() in doc["points"]
 
 
