@@ -128,6 +128,18 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
+    def wait_first_sample(self, timeout: float = 3.0) -> None:
+        """Block until the sampler has written its first row (its start-up,
+        which queries the device, is then over), or the timeout passes."""
+        if self.proc is None:
+            return
+        t_end = time.perf_counter() + timeout
+        while time.perf_counter() < t_end:
+            self.file.flush()
+            if os.path.getsize(self.file.name) > 0:
+                return
+            time.sleep(0.02)
+
     def stop(self) -> dict | None:
         if self.proc is None:
             return None
@@ -338,14 +350,17 @@ def run_ours(a):
     dev_out = torch.zeros((a.warmup + a.steps) * sl.RESULT_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     rb = sl.RESULT_BYTES
+    # the clock sampler runs through the timed region; it is started first and
+    # its start-up (device queries) has ended before the warm-up steps begin
+    clocks = ClockSampler(info["device"])
+    if rank == 0:
+        clocks.start()
+        clocks.wait_first_sample()
     sl.sl_enqueue_steps(bufs, dev_out, a.warmup, dtype=sl.SL_U32, cfg=cfg)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(info["device"])
-    if rank == 0:
-        clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record(stream)
     sl.sl_enqueue_steps(bufs, dev_out[rb * a.warmup:], a.steps, dtype=sl.SL_U32, cfg=cfg)
